@@ -1,0 +1,446 @@
+"""Benchmark of the MVP ray-march path on GB300.
+
+One step = one frame of the paper-scale workload (4096 primitives of 16^3 RGBA FP32
+voxels on an ellipsoid shell, one 667x1024 camera, dt = 0.005 over t in [1, 5]):
+rebuild the BVH (per-frame rebuild, Sec. 3.2.1) and march every pixel (Sec. 3.2.2),
+through the C ABI. Inputs are resident in HBM; L2 is flushed (a 512 MiB write)
+before every timed step and each step is timed with CUDA events on its stream.
+
+Printed: one JSON line (rank 0). Besides the headline forward FP32 figure it carries
+the BF16 / FP16 payload variants, the 512x32^3 and 32768x8^3 sweeps, and the
+differentiation workload (512 x 32^3, 4 cameras of 512x512, forward + backward).
+
+--impl reference times the CPU oracle (FP64, plain loops; the only reference this
+method has) on a bounded ray sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "paper_4096x16^3_667x1024"
+METRIC = "MVP raymarch Mrays/s fwd & fwd+bwd vs plain FP32; serving p50/p99 ms/frame"
+
+# Algorithmic work per (sample, primitive) evaluation: 8 voxel reads of 4 channels
+# (bytes by dtype) and the FP32 operations of the definition (local coordinates
+# 3x3 FMA = 18, trilinear 7 lerps x 4 channels x 3 = 84, accumulation 7).
+FLOP_PER_EVAL = 109
+GATHER_BYTES = {"f32": 128, "bf16": 64, "f16": 64}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 7:
+                try:
+                    rows.append(parts)
+                except Exception:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _frame_runner(cfg: str, seed: int, dtype: str, want_bwd: bool, torch, T, synthetic):
+    """Set up a workload on the device; returns (step(), n_rays, info)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    scene, rays, extra = synthetic.make_config(cfg, seed)
+    ctx = T.Context(dev.index)
+    t = torch.from_numpy(scene.t).to(dev)
+    q = torch.from_numpy(scene.q).to(dev)
+    s = torch.from_numpy(scene.s).to(dev)
+    p32 = torch.from_numpy(scene.payload).to(dev)
+    tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[dtype]
+    payload = p32 if dtype == "f32" else T.pack_payload(ctx, p32, tdt)
+    if dtype != "f32":
+        del p32
+    o = torch.from_numpy(rays.o).to(dev)
+    d = torch.from_numpy(rays.d).to(dev)
+    prims = T.prims_struct(t, q, s, payload)
+    rs = T.rays_struct(o, d, t_near=rays.t_near, t_far=rays.t_far, dt=rays.dt, eps_early=rays.eps_early,
+                       bg=tuple(rays.bg), width=rays.width, height=rays.height)
+    bvh = T.BVH(ctx)
+    bvh.build(prims)
+    out = torch.empty((rays.n, 4), dtype=torch.float32, device=dev)
+    saved = torch.empty(T.saved_bytes(rays.n), dtype=torch.uint8, device=dev) if want_bwd else None
+    grads = None
+    if want_bwd:
+        target = torch.from_numpy(extra["target"]).to(dev)
+        gp = torch.zeros(payload.shape, dtype=torch.float32, device=dev)
+        gt, gq, gs = torch.zeros_like(t), torch.zeros_like(q), torch.zeros_like(s)
+        grad_out = torch.zeros((rays.n, 4), dtype=torch.float32, device=dev)
+        grads = (gp, gt, gq, gs, grad_out, target)
+    ev = {"march": []}
+
+    def step(time_march=False):
+        bvh.build(prims)
+        if time_march:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+        T.raymarch_fwd(ctx, prims, bvh, rs, out=out, saved=saved)
+        if time_march:
+            e1.record()
+            ev["march"].append((e0, e1))
+        if want_bwd:
+            gp, gt, gq, gs, grad_out, target = grads
+            # photometric L2 loss (Sec. 3.3, lambda = 1): dL/dI = 2 (I - target) / R
+            torch.sub(out[:, :3], target, out=grad_out[:, :3]).mul_(2.0 / rays.n)
+            gp.zero_(), gt.zero_(), gq.zero_(), gs.zero_()
+            T.raymarch_bwd(ctx, prims, bvh, rs, saved, grad_out, gp, gt, gq, gs)
+
+    info = {"scene": scene, "rays": rays, "ctx": ctx, "prims": prims, "bvh": bvh, "rs": rs, "ev": ev,
+            "payload_bytes": payload.numel() * payload.element_size(), "out": out,
+            "host": (scene, rays)}
+    return step, rays.n, info
+
+
+def _time_steps(torch, step, steps, warmup, flush, time_march=False):
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    durs = []
+    for _ in range(steps):
+        flush.fill_(1.0)  # write 512 MiB: evicts L2 between timed steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step(time_march) if time_march else step()
+        e1.record()
+        durs.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in durs]
+
+
+def _e2e(torch, T, info, steps, warmup):
+    """Same frame through the C ABI from pinned host buffers: copy the frame's inputs
+    (poses, payload, rays) host->device, build + march, read the image back."""
+    scene, rays = info["host"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    hs = [torch.from_numpy(a).pin_memory() for a in (scene.t, scene.q, scene.s, scene.payload, rays.o, rays.d)]
+    ds = [torch.empty(h.shape, dtype=h.dtype, device=dev) for h in hs]
+    hout = torch.empty((rays.n, 4), dtype=torch.float32).pin_memory()
+    ctx, bvh = info["ctx"], info["bvh"]
+    prims = T.prims_struct(ds[0], ds[1], ds[2], ds[3])
+    rs = T.rays_struct(ds[4], ds[5], t_near=rays.t_near, t_far=rays.t_far, dt=rays.dt, width=rays.width,
+                       height=rays.height)
+    out = info["out"]
+
+    def step():
+        for h, d in zip(hs, ds):
+            d.copy_(h, non_blocking=True)
+        bvh.build(prims)
+        T.raymarch_fwd(ctx, prims, bvh, rs, out=out)
+        hout.copy_(out, non_blocking=True)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    h2d = sum(h.numel() * h.element_size() for h in hs)
+    d2h = hout.numel() * hout.element_size()
+    return {"value": rays.n / (ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": ms, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h}
+
+
+def _cpu_baseline(seconds: float = 15.0):
+    """The oracle (FP64, pruned mode, FP32 membership) on a seeded ray sample of the
+    workload, on all host cores."""
+    import oracle
+    import synthetic
+
+    oracle.build()
+    scene, rays, _ = synthetic.make_config(WORKLOAD, 0)
+    rng = np.random.default_rng(123)
+    n = 256
+    total_rays, total_s = 0, 0.0
+    while total_s < seconds:
+        sel = rng.choice(rays.n, n, replace=False)
+        sub = synthetic.Rays(o=rays.o[sel], d=rays.d[sel], t_near=rays.t_near, t_far=rays.t_far, dt=rays.dt)
+        t0 = time.perf_counter()
+        oracle.render(scene, sub)
+        dt = time.perf_counter() - t0
+        total_rays += n
+        total_s += dt
+        if dt < seconds / 8:
+            n *= 2
+    cores = os.cpu_count()
+    return {"value": total_rays / total_s / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+            "sample": f"{total_rays} seeded random pixels of the 667x1024 frame (of 683008), FP64 oracle, "
+                      f"pruned mode, {cores} OpenMP threads, {total_s:.1f} s"}
+
+
+def _traffic(kernel_key: str):
+    """DRAM bytes per launch of the march kernel from the committed ncu summary, if it
+    was taken with the current library build."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        from paper_2103_01954_gb300 import build as b
+
+        d = json.load(open(p))
+        e = d.get(kernel_key)
+        if e and e.get("source_digest") == b._digest():
+            return e.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+    return None
+
+
+def run_gpu(args):
+    import torch
+
+    import synthetic
+    from paper_2103_01954_gb300 import torch_ops as T
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)
+    peaks, peak_kind = _peaks()
+
+    # headline: FP32 forward at paper scale; each rank renders its own seeded frame
+    step, n_rays, info = _frame_runner(WORKLOAD, rank, "f32", False, torch, T, synthetic)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        durs = _time_steps(torch, step, args.steps, args.warmup, flush, time_march=True)
+    info["ctx"].sync()
+    ms = float(np.mean(durs))
+    if ws > 1:
+        import torch.distributed as dist
+
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    march_ms = float(np.mean([a.elapsed_time(b) for a, b in info["ev"]["march"]]))
+    # evaluations of one frame (the work count of the roofline)
+    n_eval = int(T.raymarch_count(info["ctx"], info["prims"], info["bvh"], info["rs"]).sum().item())
+    info["ctx"].sync()
+    value = ws * n_rays / (ms * 1e-3) / 1e6
+
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s (FMA = 2)
+    achieved = FLOP_PER_EVAL * n_eval / (march_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                "frac": round(achieved / fp32_peak, 4), "traffic": _traffic("k_march_f32"),
+                "kernel": "k_march<f32>", "march_ms": round(march_ms, 4), "evaluations": n_eval,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                "gather_GBps": round(GATHER_BYTES["f32"] * n_eval / (march_ms * 1e-3) / 1e9, 1),
+                "hbm_peak_GBps": peaks.get("hbm_gbs"), "hbm_peak_kind": peak_kind}
+    launches_per_step = 17
+    result = {"metric": METRIC, "value": round(value, 3), "unit": "Mrays/s", "n_gpus": ws, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; stands in for the paper's captures)",
+              "config": {"workload": WORKLOAD, "primitives": 4096, "payload": "16^3 RGBA f32", "rays": n_rays,
+                         "image": "667x1024", "dt": 0.005, "t_range": [1.0, 5.0], "samples_per_ray": 800,
+                         "step": "BVH rebuild + traversal + march", "l2": "flushed (512 MiB write) before each step",
+                         "parallelism": f"replicas x{ws} (each rank its own frame)"},
+              "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps}
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    if rank == 0 and not args.quick:
+        result["e2e"] = _e2e(torch, T, info, max(3, args.steps // 2), 2)
+    del info, step
+    torch.cuda.empty_cache()
+
+    variants = {}
+    if rank == 0 and not args.quick:
+        for name, cfg, dtype in (("fwd_bf16", WORKLOAD, "bf16"), ("fwd_f16", WORKLOAD, "f16"),
+                                 ("fwd_f32_512x32^3", "sweep_512x32^3_667x1024", "f32"),
+                                 ("fwd_f32_32768x8^3", "sweep_32768x8^3_667x1024", "f32"),
+                                 ("fwd_bf16_32768x8^3", "sweep_32768x8^3_667x1024", "bf16")):
+            st, nr, inf = _frame_runner(cfg, 0, dtype, False, torch, T, synthetic)
+            d = _time_steps(torch, st, args.steps, args.warmup, flush, time_march=True)
+            inf["ctx"].sync()
+            m = float(np.mean(d))
+            mm = float(np.mean([a.elapsed_time(b) for a, b in inf["ev"]["march"]]))
+            variants[name] = {"value": round(nr / (m * 1e-3) / 1e6, 3), "unit": "Mrays/s", "ms_per_step": round(m, 4),
+                              "march_ms": round(mm, 4), "workload": cfg, "payload_dtype": dtype}
+            del st, inf
+            torch.cuda.empty_cache()
+        st, nr, inf = _frame_runner("diff_512x32^3_4x512x512", 0, "f32", True, torch, T, synthetic)
+        d = _time_steps(torch, st, args.steps, args.warmup, flush)
+        inf["ctx"].sync()
+        m = float(np.mean(d))
+        variants["fwd_bwd_f32_512x32^3_4x512x512"] = {
+            "value": round(nr / (m * 1e-3) / 1e6, 3), "unit": "Mrays/s", "ms_per_step": round(m, 4),
+            "workload": "diff_512x32^3_4x512x512", "step": "BVH + forward + L2 loss grad + backward (payload + pose)"}
+        del st, inf
+        torch.cuda.empty_cache()
+        if variants.get("fwd_bf16"):
+            variants["bf16_over_f32"] = round(variants["fwd_bf16"]["value"] / value, 3)
+        result["variants"] = variants
+        if not args.no_cpu:
+            result["cpu_baseline"] = _cpu_baseline(args.cpu_seconds)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result))
+
+
+def run_reference(args):
+    """The oracle on the host cores: each step renders a bounded seeded ray sample of
+    the same workload; Mrays/s of the CPU path."""
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    import oracle
+    import synthetic
+
+    oracle.build()
+    scene, rays, _ = synthetic.make_config(WORKLOAD, 0)
+    rng = np.random.default_rng(7)
+    n = 2048
+
+    def step():
+        sel = rng.choice(rays.n, n, replace=False)
+        sub = synthetic.Rays(o=rays.o[sel], d=rays.d[sel], t_near=rays.t_near, t_far=rays.t_far, dt=rays.dt)
+        oracle.render(scene, sub)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    sec = (time.perf_counter() - t0) / args.steps
+    v = n / sec / 1e6
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "Mrays/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rays_per_step": n, "sample": "seeded random pixels"},
+            "cpu_baseline": {"value": round(v, 6), "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} seeded random pixels of the 667x1024 frame per step"},
+            "e2e": {"value": round(v, 6), "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_profile(args):
+    """Render a few frames of one workload (for ncu captures): BVH build + march,
+    and with --backward also the adjoint."""
+    import torch
+
+    import synthetic
+    from paper_2103_01954_gb300 import torch_ops as T
+
+    torch.cuda.set_device(0)
+    step, _, info = _frame_runner(args.workload, 0, args.dtype, args.backward, torch, T, synthetic)
+    for _ in range(args.frames):
+        step()
+    info["ctx"].sync()
+    torch.cuda.synchronize()
+    print(json.dumps({"profiled": args.workload, "frames": args.frames, "dtype": args.dtype,
+                      "backward": args.backward}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--quick", action="store_true", help="headline figure only")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile", action="store_true", help="render --frames frames of --workload, no timing")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--frames", type=int, default=2)
+    ap.add_argument("--backward", action="store_true")
+    args = ap.parse_args()
+    if args.profile:
+        run_profile(args)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * mvp.h -- C ABI of the GB300 ray-march library for Mixture of Volumetric
+ * Primitives (Lombardi et al., "Mixture of Volumetric Primitives for Efficient
+ * Neural Rendering", ACM TOG 40(4), 2021).
+ *
+ * The library implements the paper's rendering hot path (Sec. 3.2): a per-frame
+ * bounding volume hierarchy over moving, oriented primitives (Sec. 3.2.1, built
+ * with the data-parallel LBVH construction the paper cites), per-ray lists of the
+ * primitives each ray intersects (Sec. 3.2.1), the fixed-step ray march with
+ * trilinear payload sampling and clamped additive opacity accumulation
+ * (Sec. 3.2.2), its adjoint, payload precision conversion, and a serving loop.
+ *
+ * Conventions for every call:
+ *   - Pointers documented as "device" are CUDA device pointers owned by the
+ *     caller; the library never frees them. "host" pointers are ordinary memory.
+ *   - Opaque handles (mvp_ctx, mvp_bvh, mvp_server) are created and freed by the
+ *     library's *_create / *_destroy calls.
+ *   - Calls that take an mvp_stream are asynchronous on that stream unless their
+ *     comment says they synchronise. A NULL stream is the legacy default stream.
+ *   - Every call returns an mvp_status; nothing throws or aborts across the ABI.
+ *     Host-side argument checks return MVP_ERR_INVALID_ARG before any launch.
+ *     Errors found by a kernel (capacity overflow) are recorded in the context's
+ *     device status word and reported by the next mvp_ctx_sync on that context.
+ *     mvp_last_error() returns a thread-local message for the last failure.
+ *   - All floating-point arithmetic on the device is FP32. Payloads may be stored
+ *     as FP32, BF16 or FP16; interpolation and compositing are FP32.
+ *
+ * Geometry (Sec. 3.1.2). Primitive k has centre t_k, rotation R_k = R(q_k/|q_k|)
+ * from the quaternion q_k = (w, x, y, z), and half extents s_k > 0: a local point
+ * y in [-1,1]^3 lies at t_k + R_k diag(s_k) y in the world. Its payload is an
+ * M x M x M grid of RGBA voxels (colour and opacity density), indexed
+ * [k][z][y][x][c] with x fastest; voxel centres sit on the box corners and faces
+ * (the voxel coordinate of a local coordinate y is (y + 1)/2 * (M - 1)).
+ *
+ * Quadrature (Sec. 3.2.2). A ray o + t d (d unit) is sampled at
+ * t_i = t_near + i*dt for i in [0, n_steps), n_steps = mvp_num_steps(...). Every
+ * primitive whose box contains t_i contributes alpha_k and rgb_k (trilinear);
+ * a = dt * sum alpha_k, c = dt * sum alpha_k rgb_k, w = min(a, 1 - T),
+ * I += c * w / a, T += w. The march stops once T >= 1 - eps_early. The output is
+ * (I + (1 - A) * bg, A) with A the final T (Sec. 3.1.4 composite, with I already
+ * weighted by the accumulated opacity).
+ * Box membership of a sample is decided in FP32 with a fixed operation order
+ * (the slab interval of the ray against the box, compared with the FP32 sample
+ * time), which makes hit lists reproducible bit for bit.
+ */
+#ifndef MVP_H
+#define MVP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MVP_API __attribute__((visibility("default")))
+#else
+#define MVP_API
+#endif
+
+#define MVP_ABI_VERSION 1
+#define MVP_MAX_M 128          /* largest payload edge */
+#define MVP_MAX_STEPS 65535    /* largest n_steps per ray */
+#define MVP_MAX_PRIMS (1 << 24)
+
+typedef struct CUstream_st *mvp_stream; /* same type as cudaStream_t */
+
+typedef enum mvp_status {
+  MVP_OK = 0,
+  MVP_NOT_READY = 1,         /* a polled request has not finished yet */
+  MVP_ERR_INVALID_ARG = -1,  /* rejected on the host before any launch */
+  MVP_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+  MVP_ERR_OOM = -3,          /* a library allocation failed */
+  MVP_ERR_CAPACITY = -4,     /* a fixed capacity was exceeded (see the call) */
+  MVP_ERR_TIMEOUT = -5,      /* a bounded wait ran out */
+  MVP_ERR_DEVICE = -6        /* a kernel reported an inconsistent state */
+} mvp_status;
+
+typedef enum mvp_dtype { MVP_F32 = 0, MVP_BF16 = 1, MVP_F16 = 2 } mvp_dtype;
+
+/* Primitive set (Sec. 3.1.2). All pointers are device pointers. */
+typedef struct mvp_prims {
+  int32_t n;            /* number of primitives, 0 <= n <= MVP_MAX_PRIMS */
+  int32_t M;            /* payload edge, 2 <= M <= MVP_MAX_M */
+  int32_t dtype;        /* mvp_dtype of payload */
+  int32_t reserved;     /* must be 0 */
+  const float *t;       /* [n][3] centres */
+  const float *q;       /* [n][4] quaternions (w, x, y, z), nonzero */
+  const float *s;       /* [n][3] half extents, > 0 */
+  const void *payload;  /* [n][M][M][M][4] RGBA, x fastest; 16-byte aligned */
+} mvp_prims;
+
+/* Rays and quadrature parameters (Sec. 3.2.2). o, d are device pointers. */
+typedef struct mvp_rays {
+  int64_t n;            /* number of rays, >= 0 */
+  const float *o;       /* [n][3] origins */
+  const float *d;       /* [n][3] unit directions */
+  float t_near, t_far;  /* integration range, t_near < t_far */
+  float dt;             /* step, > 0 */
+  float eps_early;      /* stop once T >= 1 - eps_early, 0 <= eps_early < 1 */
+  float bg[3];          /* constant background colour */
+  int32_t width;        /* if width * height == n: rays form a row-major image  */
+  int32_t height;       /* and are marched in 2-D pixel tiles; else 1-D groups  */
+} mvp_rays;
+
+typedef struct mvp_ctx mvp_ctx;
+typedef struct mvp_bvh mvp_bvh;
+
+/* ---------------------------------------------------------------- basics */
+MVP_API const char *mvp_version(void);
+MVP_API const char *mvp_status_string(int status);
+/* Message of the last failed call on this thread ("" if none). */
+MVP_API const char *mvp_last_error(void);
+/* n_steps = ceil((t_far - t_near)/dt - 1e-4) computed in double from the FP32
+ * values (a sample within 1e-4*dt of t_far is not taken); 0 if t_far <= t_near. */
+MVP_API int64_t mvp_num_steps(float t_near, float t_far, float dt);
+
+/* Context: binds a device and owns the device status word. */
+MVP_API mvp_status mvp_ctx_create(int device, mvp_ctx **out);
+MVP_API void mvp_ctx_destroy(mvp_ctx *ctx);
+/* Synchronises `stream`, then reads and clears the device status word:
+ * MVP_ERR_CAPACITY if a kernel hit a capacity limit since the last sync, else
+ * MVP_OK (or MVP_ERR_CUDA if the stream reported an error). */
+MVP_API mvp_status mvp_ctx_sync(mvp_ctx *ctx, mvp_stream stream);
+
+/* ------------------------------------------------------ BVH (Sec. 3.2.1) */
+/* A BVH handle owns its device buffers and grows them as needed; reuse one
+ * handle across frames to avoid reallocation. */
+MVP_API mvp_status mvp_bvh_create(mvp_ctx *ctx, mvp_bvh **out);
+MVP_API void mvp_bvh_destroy(mvp_bvh *bvh);
+/* Rebuild the hierarchy over `prims` (the per-frame rebuild of Sec. 3.2.1):
+ * per-primitive rotation, oriented-box world bounds and 30-bit Morton code of the
+ * centre within the centres' bounds; a stable radix sort of the codes; the binary
+ * radix tree of the sorted keys (morton << 32 | k); bottom-up box refit.
+ * Reallocation (first use or larger n) synchronises the stream; a rebuild at the
+ * same or smaller n allocates nothing and only enqueues kernels. */
+MVP_API mvp_status mvp_build_bvh(mvp_ctx *ctx, const mvp_prims *prims, mvp_bvh *bvh, mvp_stream stream);
+/* Number of primitives of the last build. */
+MVP_API int32_t mvp_bvh_size(const mvp_bvh *bvh);
+/* Copy the last build to caller device buffers (any may be NULL), asynchronously:
+ * keys [n] uint64 sorted (morton << 32 | k); children [n-1][2] int32 (internal
+ * nodes 0..n-2, leaf j = node n-1+j holding primitive keys[j] & 0xffffffff);
+ * bounds [2n-1][6] float32 node boxes (lo xyz, hi xyz), slightly inflated;
+ * scene [6] float32 centre bounds used for the Morton codes. */
+MVP_API mvp_status mvp_bvh_export(mvp_ctx *ctx, const mvp_bvh *bvh, uint64_t *keys, int32_t *children,
+                          float *bounds, float *scene, mvp_stream stream);
+
+/* Per-ray hit lists (Sec. 3.2.1: "compute and store the primitives each ray
+ * intersects"). Fills CSR arrays (device): offs [n_rays + 1] int64, and for each
+ * hit the primitive id and the FP32 slab interval [tin, tout] clipped to
+ * [t_near, t_far], in traversal order within a ray. Writes at most `cap` hits;
+ * *n_hits (host) receives the total. Returns MVP_ERR_CAPACITY (with offs valid)
+ * if the total exceeds cap. Synchronises the stream. */
+MVP_API mvp_status mvp_hitlists(mvp_ctx *ctx, const mvp_prims *prims, const mvp_bvh *bvh, const mvp_rays *rays,
+                        int64_t *offs, int32_t *ids, float *tin, float *tout, int64_t cap,
+                        int64_t *n_hits, mvp_stream stream);
+
+/* ------------------------------------------ forward march (Sec. 3.2.2) */
+/* Bytes of per-ray state the forward saves for the adjoint (24 per ray). */
+MVP_API size_t mvp_saved_bytes(int64_t n_rays);
+/* Render: out_rgba [n][4] float32 device = (I + (1 - A) bg, A). `saved`
+ * (device, mvp_saved_bytes(n) bytes, nullable) receives the per-ray state the
+ * adjoint needs. `bvh` must have been built from the same prims. Rays are marched
+ * by warps over 8x4 pixel tiles; each tile gathers at most 64 primitives at once
+ * and splits its sample range when more overlap it. A single sample overlapped by
+ * more than 64 primitives across one tile records MVP_ERR_CAPACITY. */
+MVP_API mvp_status mvp_raymarch_fwd(mvp_ctx *ctx, const mvp_prims *prims, const mvp_bvh *bvh,
+                            const mvp_rays *rays, float *out_rgba, void *saved, mvp_stream stream);
+/* Same march, writing only the number of (sample, primitive) evaluations of each
+ * ray to n_eval [n] int32 device (the work count used for roofline figures). */
+MVP_API mvp_status mvp_raymarch_count(mvp_ctx *ctx, const mvp_prims *prims, const mvp_bvh *bvh,
+                              const mvp_rays *rays, int32_t *n_eval, mvp_stream stream);
+
+/* --------------------------------------------------------- adjoint */
+/* Gradients of a loss L given grad_rgba = dL/d(out_rgba) [n][4] (device),
+ * replaying the march from `saved` (written by mvp_raymarch_fwd with the same
+ * inputs). Accumulates (+=) into device FP32 buffers: g_payload [n][M][M][M][4],
+ * g_t [n][3], g_q [n][4], g_s [n][3] (any may be NULL to skip it; g_t, g_q and g_s
+ * are produced together). Pose gradients pass through an internal per-primitive
+ * FP32 buffer owned by the bvh handle. Gradient accumulation uses atomics, so the
+ * summation order (and the last bits) may vary between runs. */
+MVP_API mvp_status mvp_raymarch_bwd(mvp_ctx *ctx, const mvp_prims *prims, mvp_bvh *bvh, const mvp_rays *rays,
+                            const void *saved, const float *grad_rgba, float *g_payload, float *g_t,
+                            float *g_q, float *g_s, mvp_stream stream);
+
+/* ------------------------------------------------ precision and cameras */
+/* Convert n_values FP32 values (device) to dtype (device dst, round to nearest
+ * even); MVP_F32 copies. */
+MVP_API mvp_status mvp_pack_payload(mvp_ctx *ctx, const float *src, void *dst, int64_t n_values, int32_t dtype,
+                            mvp_stream stream);
+/* Pinhole rays of a W x H image, row-major: c2w (host, row-major 3x4 =
+ * [right down forward | eye]), focal in pixels, pixel centres at (col + 0.5,
+ * row + 0.5), principal point at the image centre. o, d: [W*H][3] device. */
+MVP_API mvp_status mvp_camera_rays(mvp_ctx *ctx, const float *c2w, float focal, int32_t width, int32_t height,
+                           float *o, float *d, mvp_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MVP_H */

@@ -9,12 +9,15 @@
  * from the product.
  *
  * Floating point: every value (positions, interpolation, compositing, gradients) is
- * FP64. Two discrete decisions depend on floating point and are taken in the
- * kernel's FP32 precision with a fixed operation order (round-to-nearest, no fused
- * multiply-add; this file is compiled with -ffp-contract=off):
+ * FP64. Three discrete decisions depend on floating point and are taken in the
+ * kernel's FP32 precision with a fixed operation order (round-to-nearest; this file
+ * is compiled with -ffp-contract=off, so a fused multiply-add happens only where
+ * fmaf is written out):
  *   - the Morton code of a primitive centre (a quantised integer), and
  *   - the ray/box slab interval that decides which primitives a ray hits and which
- *     samples fall inside a primitive ("f32spec" membership).
+ *     samples fall inside a primitive ("f32spec" membership), and
+ *   - the voxel cell (floor of the voxel coordinate) a sample falls in, which
+ *     decides where the trilinear derivative jumps.
  * The FP64 plain definition of membership (the sample's local coordinates lie in
  * [-1,1]^3) is available too; tests check that the two agree except on samples
  * within 1e-4 (local units) of a box face.
@@ -285,6 +288,7 @@ typedef struct {
   const float *t, *q, *s, *payload; /* payload FP32 [n][M][M][M][4], x fastest */
   double *R64;
   float *R32;
+  float *U32; /* [n][3][4] FP32 voxel-coordinate rows, see voxel_coord_f32 */
 } scene_t;
 
 typedef struct {
@@ -300,6 +304,34 @@ static float sample_t_f32(const march_t *m, int i) {
   return m->t_near + p;
 }
 
+/* The voxel cell of a sample is an integer decided by floating point; in the FP32
+ * decision mode it is taken with the kernel's FP32 arithmetic: per primitive
+ * hs_j = h/s_j (h = (M-1)/2), rows M_jm = hs_j R_mj and c_j = ((h - M_j0 t0) - M_j1 t1)
+ * - M_j2 t2, each operation rounded; per sample x = fma(t_i, d, o) and
+ * u_j = fma(M_j0, x0, fma(M_j1, x1, fma(M_j2, x2, c_j))). The cell is
+ * min(floor(clamp(u, 0, M-1)), M-2) and an axis where u left [0, M-1] has zero
+ * derivative. Values (weights, colours, gradients) stay FP64. */
+static void voxel_rows_f32(const float R[9], const float *t, const float *s, int M, float rows[12]) {
+  float h = 0.5f * (float)(M - 1);
+  for (int j = 0; j < 3; ++j) {
+    float hs = h / s[j];
+    float c = h;
+    for (int m = 0; m < 3; ++m) {
+      float mj = hs * R[3 * m + j];
+      rows[4 * j + m] = mj;
+      float pr = mj * t[m];
+      c = c - pr;
+    }
+    rows[4 * j + 3] = c;
+  }
+}
+
+static void voxel_coord_f32(const float rows[12], const float *o, const float *d, float ti32, float u[3]) {
+  float x0 = fmaf(ti32, d[0], o[0]), x1 = fmaf(ti32, d[1], o[1]), x2 = fmaf(ti32, d[2], o[2]);
+  for (int j = 0; j < 3; ++j)
+    u[j] = fmaf(rows[4 * j], x0, fmaf(rows[4 * j + 1], x1, fmaf(rows[4 * j + 2], x2, rows[4 * j + 3])));
+}
+
 /* Local coordinates y = diag(1/s) R^T (x - t) (R3). */
 static void local_f64(const scene_t *sc, int k, const double x[3], double y[3]) {
   const double *R = sc->R64 + 9 * k;
@@ -312,8 +344,8 @@ static void local_f64(const scene_t *sc, int k, const double x[3], double y[3]) 
  * to [0, M-1] (a no-op for samples inside the box). Optionally returns the 8 cell
  * corner voxel indices, their weights and dv/du (4 channels x 3 axes; zero along a
  * clamped axis). */
-static void trilinear(const scene_t *sc, int k, const double y[3], double v[4], int64_t cidx[8],
-                      double cw[8], double dvdu[4][3]) {
+static void trilinear(const scene_t *sc, int k, const double y[3], const float *u32, double v[4],
+                      int64_t cidx[8], double cw[8], double dvdu[4][3]) {
   int M = sc->M;
   double u[3], f[3];
   int i0[3], clamped[3];
@@ -322,8 +354,17 @@ static void trilinear(const scene_t *sc, int k, const double y[3], double v[4], 
     clamped[j] = 0;
     if (u[j] < 0.0) { u[j] = 0.0; clamped[j] = 1; }
     if (u[j] > (double)(M - 1)) { u[j] = (double)(M - 1); clamped[j] = 1; }
-    int fl = (int)floor(u[j]);
-    i0[j] = fl < M - 2 ? fl : M - 2;
+    if (u32) {  /* cell and clamp decided by the FP32 coordinate */
+      float uf = u32[j];
+      clamped[j] = !(uf >= 0.0f && uf <= (float)(M - 1));
+      if (uf < 0.0f) uf = 0.0f;
+      if (uf > (float)(M - 1)) uf = (float)(M - 1);
+      int fl = (int)uf;
+      i0[j] = fl < M - 2 ? fl : M - 2;
+    } else {
+      int fl = (int)floor(u[j]);
+      i0[j] = fl < M - 2 ? fl : M - 2;
+    }
     f[j] = u[j] - i0[j];
   }
   const float *P = sc->payload + (size_t)k * M * M * M * 4;
@@ -447,7 +488,9 @@ static void march_ray(const scene_t *sc, const march_t *m, int64_t r, int mode, 
       if (!in) continue;
       int k = pruned ? cands[e].k : e;
       double v[4];
-      trilinear(sc, k, y, v, NULL, NULL, NULL);
+      float u32[3];
+      if (f32m) voxel_coord_f32(sc->U32 + 12 * k, o, d, ti32, u32);
+      trilinear(sc, k, y, f32m ? u32 : NULL, v, NULL, NULL, NULL);
       a += v[3];
       c[0] += v[3] * v[0]; c[1] += v[3] * v[1]; c[2] += v[3] * v[2];
       res->n_eval++;
@@ -477,12 +520,17 @@ static int scene_init(scene_t *sc, int n, int M, const float *t, const float *q,
   sc->n = n; sc->M = M; sc->t = t; sc->q = q; sc->s = s; sc->payload = payload;
   sc->R64 = (double *)malloc(sizeof(double) * 9 * (size_t)(n > 0 ? n : 1));
   sc->R32 = (float *)malloc(sizeof(float) * 9 * (size_t)(n > 0 ? n : 1));
-  if (!sc->R64 || !sc->R32) return -1;
-  for (int k = 0; k < n; ++k) { rot_f64(q + 4 * k, sc->R64 + 9 * k); rot_f32spec(q + 4 * k, sc->R32 + 9 * k); }
+  sc->U32 = (float *)malloc(sizeof(float) * 12 * (size_t)(n > 0 ? n : 1));
+  if (!sc->R64 || !sc->R32 || !sc->U32) return -1;
+  for (int k = 0; k < n; ++k) {
+    rot_f64(q + 4 * k, sc->R64 + 9 * k);
+    rot_f32spec(q + 4 * k, sc->R32 + 9 * k);
+    voxel_rows_f32(sc->R32 + 9 * k, t + 3 * k, s + 3 * k, M, sc->U32 + 12 * k);
+  }
   return 0;
 }
 
-static void scene_free(scene_t *sc) { free(sc->R64); free(sc->R32); }
+static void scene_free(scene_t *sc) { free(sc->R64); free(sc->R32); free(sc->U32); }
 
 /* Render: out[r] = (I + (1 - A) bg, A) (R5); near_face, n_eval and the adjoint
  * state (i_last, i_clamp, rho, beta) are optional. Returns 0, or -1 on bad input. */
@@ -610,7 +658,9 @@ int orc_backward(int n, int M, const float *t, const float *q, const float *s, c
           int k = pruned ? cands[e].k : e;
           double v[4], cw[8], dvdu[4][3];
           int64_t cidx[8];
-          trilinear(&sc, k, y, v, cidx, cw, dvdu);
+          float u32[3];
+          if (f32m) voxel_coord_f32(sc.U32 + 12 * k, or_, dr, ti32, u32);
+          trilinear(&sc, k, y, f32m ? u32 : NULL, v, cidx, cw, dvdu);
           double galpha = dt * (ga + gc[0] * v[0] + gc[1] * v[1] + gc[2] * v[2]);
           double gv[4] = {dt * v[3] * gc[0], dt * v[3] * gc[1], dt * v[3] * gc[2], galpha};
           double *GP = g_payload + (size_t)k * M * M * M * 4;

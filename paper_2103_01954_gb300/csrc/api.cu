@@ -1,0 +1,398 @@
+// api.cu -- the C ABI declared in include/mvp.h: argument validation, handles and
+// dispatch to the kernels. Nothing here computes on the host beyond sizes.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "march.cuh"
+#include "pack.cuh"
+
+struct mvp_ctx {
+  int device = 0;
+  int *d_status = nullptr;  // device status word (STATUS_* bits)
+};
+
+struct mvp_bvh {
+  int device = 0;  // copied from the context: the handle may outlive it
+  mvp::BvhBuffers b;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+mvp_status fail(mvp_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+mvp_status cuda_fail(cudaError_t e, const char *where) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(MVP_ERR_OOM, "%s: %s", where, cudaGetErrorString(e));
+  return fail(MVP_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+mvp_status ok() { return MVP_OK; }
+
+bool finite(float v) { return isfinite(v); }
+
+mvp_status check_prims(const mvp_prims *p) {
+  if (!p) return fail(MVP_ERR_INVALID_ARG, "prims is NULL");
+  if (p->n < 0 || p->n > MVP_MAX_PRIMS) return fail(MVP_ERR_INVALID_ARG, "prims.n = %d out of range", p->n);
+  if (p->M < 2 || p->M > MVP_MAX_M) return fail(MVP_ERR_INVALID_ARG, "prims.M = %d out of [2, %d]", p->M, MVP_MAX_M);
+  if (p->dtype != MVP_F32 && p->dtype != MVP_BF16 && p->dtype != MVP_F16)
+    return fail(MVP_ERR_INVALID_ARG, "prims.dtype = %d unknown", p->dtype);
+  if (p->reserved != 0) return fail(MVP_ERR_INVALID_ARG, "prims.reserved must be 0");
+  if ((int64_t)p->n * p->M * p->M * p->M >= ((int64_t)1 << 40))
+    return fail(MVP_ERR_INVALID_ARG, "payload too large");
+  if (p->n > 0) {
+    if (!p->t || !p->q || !p->s || !p->payload) return fail(MVP_ERR_INVALID_ARG, "prims has a NULL array");
+    size_t align = p->dtype == MVP_F32 ? 16 : 8;
+    if (reinterpret_cast<uintptr_t>(p->payload) % align)
+      return fail(MVP_ERR_INVALID_ARG, "payload must be %zu-byte aligned", align);
+  }
+  return ok();
+}
+
+mvp_status check_rays(const mvp_rays *r, int64_t *n_steps) {
+  if (!r) return fail(MVP_ERR_INVALID_ARG, "rays is NULL");
+  if (r->n < 0) return fail(MVP_ERR_INVALID_ARG, "rays.n < 0");
+  if (r->n > 0 && (!r->o || !r->d)) return fail(MVP_ERR_INVALID_ARG, "rays has a NULL array");
+  if (!finite(r->t_near) || !finite(r->t_far) || !finite(r->dt) || !finite(r->eps_early))
+    return fail(MVP_ERR_INVALID_ARG, "rays parameters must be finite");
+  if (!(r->dt > 0.0f)) return fail(MVP_ERR_INVALID_ARG, "rays.dt must be > 0");
+  if (!(r->t_far > r->t_near)) return fail(MVP_ERR_INVALID_ARG, "rays.t_far must be > t_near");
+  if (!(r->eps_early >= 0.0f && r->eps_early < 1.0f)) return fail(MVP_ERR_INVALID_ARG, "rays.eps_early not in [0, 1)");
+  if (r->width < 0 || r->height < 0) return fail(MVP_ERR_INVALID_ARG, "rays.width/height < 0");
+  for (int c = 0; c < 3; ++c)
+    if (!finite(r->bg[c])) return fail(MVP_ERR_INVALID_ARG, "rays.bg must be finite");
+  int64_t ns = mvp_num_steps(r->t_near, r->t_far, r->dt);
+  if (ns > MVP_MAX_STEPS) return fail(MVP_ERR_INVALID_ARG, "n_steps = %lld exceeds %d", (long long)ns, MVP_MAX_STEPS);
+  *n_steps = ns;
+  return ok();
+}
+
+mvp_status check_bvh(const mvp_bvh *bvh, const mvp_prims *p) {
+  if (!bvh) return fail(MVP_ERR_INVALID_ARG, "bvh is NULL");
+  if (bvh->b.n != p->n || (p->n > 0 && bvh->b.M != p->M))
+    return fail(MVP_ERR_INVALID_ARG, "bvh was built for n=%d M=%d, prims have n=%d M=%d", bvh->b.n, bvh->b.M, p->n,
+                p->M);
+  return ok();
+}
+
+mvp::MarchArgs march_args(mvp_ctx *ctx, const mvp_prims *p, const mvp_bvh *bvh, const mvp_rays *r, int64_t ns) {
+  mvp::MarchArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n_prims = p->n;
+  a.M = p->M;
+  a.dtype = p->dtype;
+  a.payload = p->payload;
+  a.nodes = bvh->b.nodes;
+  a.pose = bvh->b.pose;
+  a.xf = bvh->b.xf;
+  a.geom = mvp::make_tile_geom(r->n, r->width, r->height);
+  a.o = r->o;
+  a.d = r->d;
+  a.t_near = r->t_near;
+  a.t_far = r->t_far;
+  a.dt = r->dt;
+  a.stop_T = (float)(1.0 - (double)r->eps_early);
+  a.bg[0] = r->bg[0];
+  a.bg[1] = r->bg[1];
+  a.bg[2] = r->bg[2];
+  a.n_steps = (int)ns;
+  a.status = ctx->d_status;
+  return a;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    (void)cudaGetLastError();  // a pending error of other code is not this call's
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char *mvp_version(void) { return "mvp-gb300 1.0 (abi 1, sm_103a)"; }
+
+const char *mvp_status_string(int s) {
+  switch (s) {
+    case MVP_OK: return "MVP_OK";
+    case MVP_NOT_READY: return "MVP_NOT_READY";
+    case MVP_ERR_INVALID_ARG: return "MVP_ERR_INVALID_ARG";
+    case MVP_ERR_CUDA: return "MVP_ERR_CUDA";
+    case MVP_ERR_OOM: return "MVP_ERR_OOM";
+    case MVP_ERR_CAPACITY: return "MVP_ERR_CAPACITY";
+    case MVP_ERR_TIMEOUT: return "MVP_ERR_TIMEOUT";
+    case MVP_ERR_DEVICE: return "MVP_ERR_DEVICE";
+  }
+  return "MVP_UNKNOWN_STATUS";
+}
+
+const char *mvp_last_error(void) { return g_err.c_str(); }
+
+int64_t mvp_num_steps(float t_near, float t_far, float dt) {
+  if (!(dt > 0.0f) || !(t_far > t_near)) return 0;
+  double x = ((double)t_far - (double)t_near) / (double)dt;
+  double c = ceil(x - 1e-4);
+  return c > 0 ? (int64_t)c : 0;
+}
+
+mvp_status mvp_ctx_create(int device, mvp_ctx **out) {
+  if (!out) return fail(MVP_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= count) return fail(MVP_ERR_INVALID_ARG, "device %d of %d", device, count);
+  DeviceGuard g(device);
+  mvp_ctx *c = new (std::nothrow) mvp_ctx();
+  if (!c) return fail(MVP_ERR_OOM, "host allocation");
+  c->device = device;
+  e = cudaMalloc(&c->d_status, sizeof(int));
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaMalloc(status)");
+  }
+  e = cudaMemset(c->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaFree(c->d_status);
+    delete c;
+    return cuda_fail(e, "cudaMemset(status)");
+  }
+  *out = c;
+  return ok();
+}
+
+void mvp_ctx_destroy(mvp_ctx *ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaFree(ctx->d_status);
+  delete ctx;
+}
+
+mvp_status mvp_ctx_sync(mvp_ctx *ctx, mvp_stream stream) {
+  if (!ctx) return fail(MVP_ERR_INVALID_ARG, "ctx is NULL");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  int st = 0;
+  e = cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read status");
+  if (st) {
+    cudaMemset(ctx->d_status, 0, sizeof(int));
+    if (st & mvp::STATUS_CAPACITY)
+      return fail(MVP_ERR_CAPACITY, "a kernel exceeded a capacity limit (more than %d primitives overlap one sample "
+                                    "of a ray tile, or the traversal stack of %d entries overflowed)",
+                  mvp::MARCH_CAP, mvp::STACK);
+    return fail(MVP_ERR_DEVICE, "device status word 0x%x", st);
+  }
+  return ok();
+}
+
+mvp_status mvp_bvh_create(mvp_ctx *ctx, mvp_bvh **out) {
+  if (!ctx || !out) return fail(MVP_ERR_INVALID_ARG, "NULL argument");
+  mvp_bvh *b = new (std::nothrow) mvp_bvh();
+  if (!b) return fail(MVP_ERR_OOM, "host allocation");
+  b->device = ctx->device;
+  *out = b;
+  return ok();
+}
+
+void mvp_bvh_destroy(mvp_bvh *bvh) {
+  if (!bvh) return;
+  DeviceGuard g(bvh->device);
+  mvp::bvh_release(bvh->b);
+  delete bvh;
+}
+
+int32_t mvp_bvh_size(const mvp_bvh *bvh) { return bvh ? bvh->b.n : -1; }
+
+mvp_status mvp_build_bvh(mvp_ctx *ctx, const mvp_prims *prims, mvp_bvh *bvh, mvp_stream stream) {
+  if (!ctx || !bvh) return fail(MVP_ERR_INVALID_ARG, "NULL argument");
+  mvp_status s = check_prims(prims);
+  if (s) return s;
+  DeviceGuard g(ctx->device);
+  if (prims->n > bvh->b.cap) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sync before BVH growth");
+    e = mvp::bvh_reserve(bvh->b, prims->n);
+    if (e != cudaSuccess) return cuda_fail(e, "BVH allocation");
+  }
+  cudaError_t e = mvp::bvh_build(bvh->b, prims->t, prims->q, prims->s, prims->n, prims->M, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "BVH build launch");
+  return ok();
+}
+
+mvp_status mvp_bvh_export(mvp_ctx *ctx, const mvp_bvh *bvh, uint64_t *keys, int32_t *children, float *bounds,
+                          float *scene, mvp_stream stream) {
+  if (!ctx || !bvh) return fail(MVP_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = mvp::bvh_export(bvh->b, keys, children, bounds, scene, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "BVH export");
+  return ok();
+}
+
+size_t mvp_saved_bytes(int64_t n_rays) { return n_rays > 0 ? (size_t)n_rays * sizeof(mvp::Saved) : 0; }
+
+mvp_status mvp_raymarch_fwd(mvp_ctx *ctx, const mvp_prims *prims, const mvp_bvh *bvh, const mvp_rays *rays,
+                            float *out_rgba, void *saved, mvp_stream stream) {
+  if (!ctx) return fail(MVP_ERR_INVALID_ARG, "ctx is NULL");
+  int64_t ns = 0;
+  mvp_status s;
+  if ((s = check_prims(prims)) || (s = check_rays(rays, &ns)) || (s = check_bvh(bvh, prims))) return s;
+  if (rays->n > 0 && !out_rgba) return fail(MVP_ERR_INVALID_ARG, "out_rgba is NULL");
+  if (reinterpret_cast<uintptr_t>(out_rgba) % 16) return fail(MVP_ERR_INVALID_ARG, "out_rgba must be 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(saved) % 8) return fail(MVP_ERR_INVALID_ARG, "saved must be 8-byte aligned");
+  if (rays->n == 0) return ok();
+  DeviceGuard g(ctx->device);
+  mvp::MarchArgs a = march_args(ctx, prims, bvh, rays, ns);
+  a.out = out_rgba;
+  a.saved = reinterpret_cast<mvp::Saved *>(saved);
+  cudaError_t e = mvp::launch_march(a, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "march launch");
+  return ok();
+}
+
+mvp_status mvp_raymarch_count(mvp_ctx *ctx, const mvp_prims *prims, const mvp_bvh *bvh, const mvp_rays *rays,
+                              int32_t *n_eval, mvp_stream stream) {
+  if (!ctx) return fail(MVP_ERR_INVALID_ARG, "ctx is NULL");
+  int64_t ns = 0;
+  mvp_status s;
+  if ((s = check_prims(prims)) || (s = check_rays(rays, &ns)) || (s = check_bvh(bvh, prims))) return s;
+  if (rays->n > 0 && !n_eval) return fail(MVP_ERR_INVALID_ARG, "n_eval is NULL");
+  if (rays->n == 0) return ok();
+  DeviceGuard g(ctx->device);
+  mvp::MarchArgs a = march_args(ctx, prims, bvh, rays, ns);
+  a.n_eval = n_eval;
+  cudaError_t e = mvp::launch_march(a, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "count launch");
+  return ok();
+}
+
+mvp_status mvp_raymarch_bwd(mvp_ctx *ctx, const mvp_prims *prims, mvp_bvh *bvh, const mvp_rays *rays,
+                            const void *saved, const float *grad_rgba, float *g_payload, float *g_t, float *g_q,
+                            float *g_s, mvp_stream stream) {
+  if (!ctx) return fail(MVP_ERR_INVALID_ARG, "ctx is NULL");
+  int64_t ns = 0;
+  mvp_status s;
+  if ((s = check_prims(prims)) || (s = check_rays(rays, &ns)) || (s = check_bvh(bvh, prims))) return s;
+  bool pose = g_t || g_q || g_s;
+  if (pose && !(g_t && g_q && g_s)) return fail(MVP_ERR_INVALID_ARG, "g_t, g_q and g_s go together");
+  if (rays->n > 0 && (!saved || !grad_rgba)) return fail(MVP_ERR_INVALID_ARG, "saved and grad_rgba are required");
+  if (reinterpret_cast<uintptr_t>(g_payload) % 16 || reinterpret_cast<uintptr_t>(grad_rgba) % 16 ||
+      reinterpret_cast<uintptr_t>(saved) % 8)
+    return fail(MVP_ERR_INVALID_ARG, "g_payload and grad_rgba must be 16-byte aligned, saved 8-byte aligned");
+  if (rays->n == 0 || prims->n == 0) return ok();
+  DeviceGuard g(ctx->device);
+  mvp::BwdArgs b;
+  b.m = march_args(ctx, prims, bvh, rays, ns);
+  b.saved = reinterpret_cast<const mvp::Saved *>(saved);
+  b.grad = grad_rgba;
+  b.g_payload = g_payload;
+  b.gmc = pose ? bvh->b.gmc : nullptr;
+  cudaError_t e = mvp::launch_backward(b, prims->t, prims->q, prims->s, g_t, g_q, g_s, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+  return ok();
+}
+
+mvp_status mvp_hitlists(mvp_ctx *ctx, const mvp_prims *prims, const mvp_bvh *bvh, const mvp_rays *rays,
+                        int64_t *offs, int32_t *ids, float *tin, float *tout, int64_t cap, int64_t *n_hits,
+                        mvp_stream stream) {
+  if (!ctx || !n_hits) return fail(MVP_ERR_INVALID_ARG, "NULL argument");
+  int64_t ns = 0;
+  mvp_status s;
+  if ((s = check_prims(prims)) || (s = check_rays(rays, &ns)) || (s = check_bvh(bvh, prims))) return s;
+  if (!offs) return fail(MVP_ERR_INVALID_ARG, "offs is NULL");
+  if (cap > 0 && (!ids || !tin || !tout)) return fail(MVP_ERR_INVALID_ARG, "ids/tin/tout are NULL");
+  DeviceGuard g(ctx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  mvp::HitArgs a;
+  memset(&a, 0, sizeof(a));
+  a.n_prims = prims->n;
+  a.nodes = bvh->b.nodes;
+  a.pose = bvh->b.pose;
+  a.geom = mvp::make_tile_geom(rays->n, rays->width, rays->height);
+  a.o = rays->o;
+  a.d = rays->d;
+  a.t_near = rays->t_near;
+  a.t_far = rays->t_far;
+  a.offs = offs;
+  a.ids = ids;
+  a.tin = tin;
+  a.tout = tout;
+  a.cap = cap;
+  a.status = ctx->d_status;
+  int64_t *counts = nullptr;
+  cudaError_t e = cudaMallocAsync(&counts, sizeof(int64_t) * (size_t)(rays->n > 0 ? rays->n : 1), st);
+  if (e != cudaSuccess) return cuda_fail(e, "hit-list scratch");
+  cudaMemsetAsync(counts, 0, sizeof(int64_t) * (size_t)(rays->n > 0 ? rays->n : 1), st);
+  e = mvp::launch_hits(a, counts, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(n_hits, offs + rays->n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(counts, st);
+    return cuda_fail(e, "hit-list count");
+  }
+  if (cap > 0) {
+    e = mvp::launch_hits_fill(a, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  cudaFreeAsync(counts, st);
+  if (e != cudaSuccess) return cuda_fail(e, "hit-list fill");
+  if ((s = mvp_ctx_sync(ctx, stream))) return s;
+  if (*n_hits > cap) return fail(MVP_ERR_CAPACITY, "%lld hits exceed cap %lld", (long long)*n_hits, (long long)cap);
+  return ok();
+}
+
+mvp_status mvp_pack_payload(mvp_ctx *ctx, const float *src, void *dst, int64_t n_values, int32_t dtype,
+                            mvp_stream stream) {
+  if (!ctx) return fail(MVP_ERR_INVALID_ARG, "ctx is NULL");
+  if (n_values < 0) return fail(MVP_ERR_INVALID_ARG, "n_values < 0");
+  if (dtype != MVP_F32 && dtype != MVP_BF16 && dtype != MVP_F16) return fail(MVP_ERR_INVALID_ARG, "dtype unknown");
+  if (n_values > 0 && (!src || !dst)) return fail(MVP_ERR_INVALID_ARG, "NULL buffer");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = mvp::launch_pack(src, dst, n_values, dtype, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "pack launch");
+  return ok();
+}
+
+mvp_status mvp_camera_rays(mvp_ctx *ctx, const float *c2w, float focal, int32_t width, int32_t height, float *o,
+                           float *d, mvp_stream stream) {
+  if (!ctx || !c2w) return fail(MVP_ERR_INVALID_ARG, "NULL argument");
+  if (width < 0 || height < 0 || !(focal > 0.0f) || !finite(focal))
+    return fail(MVP_ERR_INVALID_ARG, "bad camera size or focal");
+  if ((int64_t)width * height > 0 && (!o || !d)) return fail(MVP_ERR_INVALID_ARG, "NULL ray buffer");
+  mvp::Cam c;
+  for (int i = 0; i < 12; ++i) {
+    if (!finite(c2w[i])) return fail(MVP_ERR_INVALID_ARG, "c2w must be finite");
+    c.m[i] = c2w[i];
+  }
+  c.focal = focal;
+  c.width = width;
+  c.height = height;
+  DeviceGuard g(ctx->device);
+  cudaError_t e = mvp::launch_camera(c, o, d, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "camera launch");
+  return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,266 @@
+// backward.cu -- adjoint of the ray march (Sec. 3.2.2: the additive accumulation
+// lets the backward pass replay samples instead of storing the per-sample graph).
+//
+// With S the clamped sample of a ray (if any), rho = c_S/a_S and beta = (1-T_S)/a_S
+// saved by the forward, and gI = dL/dI~, gA = dL/dA - gI.bg:
+//   no clamp : dL/da_i = gA,              dL/dc_i = gI        (i <= i_last)
+//   i < S    : dL/da_i = -gI.rho,         dL/dc_i = gI
+//   i = S    : dL/da_S = -(gI.rho) beta,  dL/dc_S = gI beta
+// These do not depend on the other samples, so the replay can run primitive by
+// primitive: for each window entry (warp-uniform) and each of its samples, the
+// lanes inside recompute the trilinear RGBA, scatter
+//   dL/dalpha = dt (dL/da + dL/dc . rgb), dL/drgb = dt alpha dL/dc
+// to the 8 cell voxels (float4 atomics), and accumulate dL/du (u = voxel
+// coordinate) times p = x - t_k and dL/du itself in registers; one warp reduction
+// per entry adds those 12 sums to the primitive's accumulator. A per-primitive
+// kernel then maps them to dL/dt, dL/dq, dL/ds through u = diag(h/s) R^T p + h.
+#include "march.cuh"
+
+namespace mvp {
+
+template <int DT, int CAP>
+__global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const MarchArgs &a = b.m;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  TileShared<CAP> &sh = reinterpret_cast<TileShared<CAP> *>(smem_raw)[warp];
+  const int64_t wt = (int64_t)blockIdx.x * TILE_WARPS + warp;
+  if (wt >= a.geom.n_warp_tiles) return;
+  LaneRay L;
+  load_lane_ray(L, a.o, a.d, tile_ray(a.geom, wt, lane));
+  const bool valid = L.r >= 0;
+  if (__ballot_sync(FULL, valid) == 0) return;
+
+  // per-ray adjoint constants
+  int i_last = -1, i_clamp = -1;
+  float ga_pre = 0.0f, gcr = 0.0f, gcg = 0.0f, gcb = 0.0f;
+  float ga_s = 0.0f, gsr = 0.0f, gsg = 0.0f, gsb = 0.0f;
+  if (valid) {
+    const Saved S = b.saved[L.r];
+    const float4 g = reinterpret_cast<const float4 *>(b.grad)[L.r];
+    i_last = S.i_last;
+    i_clamp = S.i_clamp;
+    gcr = g.x;
+    gcg = g.y;
+    gcb = g.z;
+    if (i_clamp < 0) {
+      ga_pre = g.w - (g.x * a.bg[0] + g.y * a.bg[1] + g.z * a.bg[2]);
+    } else {
+      const float grho = g.x * S.rho_r + g.y * S.rho_g + g.z * S.rho_b;
+      ga_pre = -grho;
+      ga_s = -grho * S.beta;
+      gsr = g.x * S.beta;
+      gsg = g.y * S.beta;
+      gsb = g.z * S.beta;
+    }
+  }
+  if (a.n_prims <= 0 || a.n_steps <= 0) return;
+  Packet P;
+  make_packet(P, valid, L.o, L.d, a.t_far);
+  const int M = a.M, M2 = M * M;
+  const float Mm1 = (float)(M - 1);
+  const int64_t M3 = (int64_t)M2 * M;
+  const int max_last = __reduce_max_sync(FULL, i_last);
+
+  int w0 = 0, wlen = a.n_steps;
+  while (w0 <= max_last) {
+    int w1 = min(a.n_steps, w0 + wlen);
+    int ne = build_window<CAP>(sh, a.nodes, a.pose, a.xf, a.n_prims, P, L, valid ? i_last : -1, a.t_near,
+                               a.t_far, a.dt, a.n_steps, w0, w1);
+    if (ne < 0) {
+      if (w1 - w0 == 1) {
+        if (lane == 0) atomicOr(a.status, STATUS_CAPACITY);
+        return;
+      }
+      wlen = (w1 - w0 + 1) >> 1;
+      continue;
+    }
+    for (int e = 0; e < ne; ++e) {
+      const int k = sh.ek[e];
+      const Xform X = sh.exf[e];
+      const uint32_t rg = sh.erng[e][lane];
+      const int lo = (int)(rg & 0xffffu), hi = (int)(rg >> 16);
+      const float4 tk = __ldg(reinterpret_cast<const float4 *>(a.pose + k) + 2);  // {R22, t0, t1, t2}
+      float acc[12];
+#pragma unroll
+      for (int c = 0; c < 12; ++c) acc[c] = 0.0f;
+      const int e_lo = sh.elo[e], e_hi = sh.ehi[e];
+      for (int i = e_lo; i <= e_hi; ++i) {
+        if (i < lo || i > hi) continue;
+        const float ti = sample_t(a.t_near, a.dt, i);
+        const float x0 = fmaf(ti, L.d[0], L.o[0]);
+        const float x1 = fmaf(ti, L.d[1], L.o[1]);
+        const float x2 = fmaf(ti, L.d[2], L.o[2]);
+        float ux = fmaf(X.r0.x, x0, fmaf(X.r0.y, x1, fmaf(X.r0.z, x2, X.r0.w)));
+        float uy = fmaf(X.r1.x, x0, fmaf(X.r1.y, x1, fmaf(X.r1.z, x2, X.r1.w)));
+        float uz = fmaf(X.r2.x, x0, fmaf(X.r2.y, x1, fmaf(X.r2.z, x2, X.r2.w)));
+        const bool kx = ux >= 0.0f && ux <= Mm1, ky = uy >= 0.0f && uy <= Mm1, kz = uz >= 0.0f && uz <= Mm1;
+        ux = fminf(fmaxf(ux, 0.0f), Mm1);
+        uy = fminf(fmaxf(uy, 0.0f), Mm1);
+        uz = fminf(fmaxf(uz, 0.0f), Mm1);
+        const int ix = min((int)ux, M - 2), iy = min((int)uy, M - 2), iz = min((int)uz, M - 2);
+        const float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
+        const int64_t v = (int64_t)k * M3 + (int64_t)(iz * M2 + iy * M + ix);
+        const float4 c000 = Voxel<DT>::load(a.payload, v);
+        const float4 c001 = Voxel<DT>::load(a.payload, v + 1);
+        const float4 c010 = Voxel<DT>::load(a.payload, v + M);
+        const float4 c011 = Voxel<DT>::load(a.payload, v + M + 1);
+        const float4 c100 = Voxel<DT>::load(a.payload, v + M2);
+        const float4 c101 = Voxel<DT>::load(a.payload, v + M2 + 1);
+        const float4 c110 = Voxel<DT>::load(a.payload, v + M2 + M);
+        const float4 c111 = Voxel<DT>::load(a.payload, v + M2 + M + 1);
+        const float4 c00 = lerp4(c000, c001, fx), c01 = lerp4(c010, c011, fx);
+        const float4 c10 = lerp4(c100, c101, fx), c11 = lerp4(c110, c111, fx);
+        const float4 c0 = lerp4(c00, c01, fy), c1 = lerp4(c10, c11, fy);
+        const float4 val = lerp4(c0, c1, fz);
+        const bool at_clamp = i == i_clamp;
+        const float ga = at_clamp ? ga_s : ga_pre;
+        const float gr = at_clamp ? gsr : gcr, gg = at_clamp ? gsg : gcg, gb = at_clamp ? gsb : gcb;
+        // dL/d(rgba) of this primitive's sample
+        const float4 gv = make_float4(a.dt * val.w * gr, a.dt * val.w * gg, a.dt * val.w * gb,
+                                      a.dt * (ga + gr * val.x + gg * val.y + gb * val.z));
+        if (b.g_payload) {
+          float4 *G = reinterpret_cast<float4 *>(b.g_payload);
+          const float wx0 = 1.0f - fx, wy0 = 1.0f - fy, wz0 = 1.0f - fz;
+          const float w00 = wy0 * wz0, w01 = fy * wz0, w10 = wy0 * fz, w11 = fy * fz;
+#define MVP_SCATTER(off, WGT)                                                                    \
+  atomicAdd(G + v + (off), make_float4((WGT) * gv.x, (WGT) * gv.y, (WGT) * gv.z, (WGT) * gv.w))
+          MVP_SCATTER(0, wx0 * w00);
+          MVP_SCATTER(1, fx * w00);
+          MVP_SCATTER(M, wx0 * w01);
+          MVP_SCATTER(M + 1, fx * w01);
+          MVP_SCATTER(M2, wx0 * w10);
+          MVP_SCATTER(M2 + 1, fx * w10);
+          MVP_SCATTER(M2 + M, wx0 * w11);
+          MVP_SCATTER(M2 + M + 1, fx * w11);
+#undef MVP_SCATTER
+        }
+        if (b.gmc) {
+          // dval/du along each axis (zero along an axis where u was clamped)
+          const float4 dx0 = lerp4(make_float4(c001.x - c000.x, c001.y - c000.y, c001.z - c000.z, c001.w - c000.w),
+                                   make_float4(c011.x - c010.x, c011.y - c010.y, c011.z - c010.z, c011.w - c010.w), fy);
+          const float4 dx1 = lerp4(make_float4(c101.x - c100.x, c101.y - c100.y, c101.z - c100.z, c101.w - c100.w),
+                                   make_float4(c111.x - c110.x, c111.y - c110.y, c111.z - c110.z, c111.w - c110.w), fy);
+          const float4 dvx = lerp4(dx0, dx1, fz);
+          const float4 dvy = lerp4(make_float4(c01.x - c00.x, c01.y - c00.y, c01.z - c00.z, c01.w - c00.w),
+                                   make_float4(c11.x - c10.x, c11.y - c10.y, c11.z - c10.z, c11.w - c10.w), fz);
+          const float4 dvz = make_float4(c1.x - c0.x, c1.y - c0.y, c1.z - c0.z, c1.w - c0.w);
+          const float gux = kx ? gv.x * dvx.x + gv.y * dvx.y + gv.z * dvx.z + gv.w * dvx.w : 0.0f;
+          const float guy = ky ? gv.x * dvy.x + gv.y * dvy.y + gv.z * dvy.z + gv.w * dvy.w : 0.0f;
+          const float guz = kz ? gv.x * dvz.x + gv.y * dvz.y + gv.z * dvz.z + gv.w * dvz.w : 0.0f;
+          const float p0 = x0 - tk.y, p1 = x1 - tk.z, p2 = x2 - tk.w;
+          acc[0] = fmaf(gux, p0, acc[0]);
+          acc[1] = fmaf(gux, p1, acc[1]);
+          acc[2] = fmaf(gux, p2, acc[2]);
+          acc[3] = fmaf(guy, p0, acc[3]);
+          acc[4] = fmaf(guy, p1, acc[4]);
+          acc[5] = fmaf(guy, p2, acc[5]);
+          acc[6] = fmaf(guz, p0, acc[6]);
+          acc[7] = fmaf(guz, p1, acc[7]);
+          acc[8] = fmaf(guz, p2, acc[8]);
+          acc[9] += gux;
+          acc[10] += guy;
+          acc[11] += guz;
+        }
+      }
+      if (b.gmc) {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = warp_sum(acc[c]);
+        if (lane < 12) {
+          float mine = acc[0];
+#pragma unroll
+          for (int c = 1; c < 12; ++c)
+            if (lane == c) mine = acc[c];
+          if (mine != 0.0f) atomicAdd(b.gmc + 12 * (int64_t)k + lane, mine);
+        }
+      }
+    }
+    w0 = w1;
+    wlen = min(a.n_steps, wlen * 2);
+  }
+}
+
+// Map the 12 accumulators of each primitive to pose gradients (+=):
+// u = Mx p + h with Mx_jm = h R_mj / s_j and p = x - t, A_jm = sum dL/du_j p_m,
+// g_j = sum dL/du_j:  dL/dt_m = -sum_j Mx_jm g_j;  dL/dR_mj = A_jm h / s_j;
+// dL/ds_j = -sum_m A_jm Mx_jm / s_j;  dL/dq through R(q/|q|).
+__global__ void k_pose_grads(const float *__restrict__ gmc, const Xform *__restrict__ xf,
+                             const Pose *__restrict__ pose, const float *__restrict__ q, int n, int M,
+                             float *__restrict__ g_t, float *__restrict__ g_q, float *__restrict__ g_s) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float *A = gmc + 12 * (int64_t)k;
+  const Xform X = xf[k];
+  const float Mx[3][3] = {{X.r0.x, X.r0.y, X.r0.z}, {X.r1.x, X.r1.y, X.r1.z}, {X.r2.x, X.r2.y, X.r2.z}};
+  const Pose P = pose[k];
+  const float s[3] = {P.p3.x, P.p3.y, P.p3.z};
+  const float h = 0.5f * (float)(M - 1);
+  float G[9];  // dL/dR, row-major
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    float gt = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gt -= Mx[j][m] * A[9 + j];
+    g_t[3 * k + m] += gt;
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    float gs = 0.0f;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      G[3 * m + j] = A[3 * j + m] * h / s[j];
+      gs -= A[3 * j + m] * Mx[j][m];
+    }
+    g_s[3 * k + j] += gs / s[j];
+  }
+  float w = q[4 * k], x = q[4 * k + 1], y = q[4 * k + 2], z = q[4 * k + 3];
+  const float nrm = sqrtf(w * w + x * x + y * y + z * z);
+  w /= nrm; x /= nrm; y /= nrm; z /= nrm;
+  const float gw = G[1] * (-2 * z) + G[2] * (2 * y) + G[3] * (2 * z) + G[5] * (-2 * x) + G[6] * (-2 * y) + G[7] * (2 * x);
+  const float gx = G[1] * (2 * y) + G[2] * (2 * z) + G[3] * (2 * y) + G[4] * (-4 * x) + G[5] * (-2 * w) +
+                   G[6] * (2 * z) + G[7] * (2 * w) + G[8] * (-4 * x);
+  const float gy = G[0] * (-4 * y) + G[1] * (2 * x) + G[2] * (2 * w) + G[3] * (2 * x) + G[5] * (2 * z) +
+                   G[6] * (-2 * w) + G[7] * (2 * z) + G[8] * (-4 * y);
+  const float gz = G[0] * (-4 * z) + G[1] * (-2 * w) + G[2] * (2 * x) + G[3] * (2 * w) + G[4] * (-4 * z) +
+                   G[5] * (2 * y) + G[6] * (2 * x) + G[7] * (2 * y);
+  const float dot = w * gw + x * gx + y * gy + z * gz;
+  g_q[4 * k] += (gw - w * dot) / nrm;
+  g_q[4 * k + 1] += (gx - x * dot) / nrm;
+  g_q[4 * k + 2] += (gy - y * dot) / nrm;
+  g_q[4 * k + 3] += (gz - z * dot) / nrm;
+}
+
+template <int DT, int CAP>
+static cudaError_t launch_bwd_t(const BwdArgs &b, cudaStream_t st) {
+  size_t smem = sizeof(TileShared<CAP>) * TILE_WARPS;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_backward<DT, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int64_t blocks = (b.m.geom.n_warp_tiles + TILE_WARPS - 1) / TILE_WARPS;
+  if (blocks > 0) k_backward<DT, CAP><<<(unsigned)blocks, TILE_WARPS * 32, smem, st>>>(b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const BwdArgs &b, const float *t, const float *q, const float *s, float *g_t,
+                            float *g_q, float *g_s, cudaStream_t st) {
+  (void)t;
+  (void)s;
+  if (b.gmc) cudaMemsetAsync(b.gmc, 0, sizeof(float) * 12 * (size_t)b.m.n_prims, st);
+  cudaError_t e = cudaSuccess;
+  switch (b.m.dtype) {
+    case MVP_F32: e = launch_bwd_t<MVP_F32, MARCH_CAP>(b, st); break;
+    case MVP_BF16: e = launch_bwd_t<MVP_BF16, MARCH_CAP>(b, st); break;
+    case MVP_F16: e = launch_bwd_t<MVP_F16, MARCH_CAP>(b, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  if (b.gmc && b.m.n_prims > 0)
+    k_pose_grads<<<(b.m.n_prims + 255) / 256, 256, 0, st>>>(b.gmc, b.m.xf, b.m.pose, q, b.m.n_prims, b.m.M, g_t,
+                                                             g_q, g_s);
+  return cudaGetLastError();
+}
+
+}  // namespace mvp

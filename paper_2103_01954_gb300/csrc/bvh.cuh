@@ -1,0 +1,33 @@
+// bvh.cuh -- device buffers of a per-frame LBVH and the build entry points.
+#pragma once
+
+#include "common.cuh"
+
+namespace mvp {
+
+struct BvhBuffers {
+  char *base = nullptr;
+  size_t bytes = 0;
+  int cap = 0;  // primitives the buffers hold
+  int n = 0;    // primitives of the last build
+  int M = 0;    // payload edge of the last build (the march transform depends on it)
+  float *scene = nullptr;  // [6] centre bounds
+  Pose *pose = nullptr;    // [n]
+  Xform *xf = nullptr;     // [n]
+  float4 *pbox = nullptr;  // [n][2] world boxes per primitive
+  uint32_t *keys_a = nullptr, *keys_b = nullptr;  // Morton codes (sorted result in keys_a)
+  int *vals_a = nullptr, *vals_b = nullptr;       // primitive ids (sorted result in vals_a)
+  int *counts = nullptr;   // radix digit counts [256][blocks]
+  Node *nodes = nullptr;   // [2n-1]
+  int *parent = nullptr;   // [2n-1]
+  int *flags = nullptr;    // [n-1] refit arrival counters
+  float *gmc = nullptr;    // [n][12] adjoint accumulators of the march transform
+};
+
+cudaError_t bvh_reserve(BvhBuffers &b, int n);
+void bvh_release(BvhBuffers &b);
+cudaError_t bvh_build(BvhBuffers &b, const float *t, const float *q, const float *s, int n, int M, cudaStream_t st);
+cudaError_t bvh_export(const BvhBuffers &b, uint64_t *keys, int32_t *children, float *bounds, float *scene,
+                       cudaStream_t st);
+
+}  // namespace mvp

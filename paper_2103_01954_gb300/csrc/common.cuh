@@ -1,0 +1,214 @@
+// common.cuh -- shared device definitions of the MVP ray-march library.
+//
+// Discrete decisions (Morton codes, ray/box membership) use explicit
+// round-to-nearest intrinsics (__fmul_rn, __fadd_rn, __fdiv_rn, __fsqrt_rn), which
+// the compiler never contracts into FMA, so their results are fixed bit for bit by
+// the operation order written here. Everything else may use FMA.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mvp.h"
+
+namespace mvp {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Device status word bits.
+constexpr int STATUS_CAPACITY = 1;
+constexpr int STATUS_DEVICE = 2;
+
+// Per-primitive pose as used by the membership test: R (row-major, R[3*i+j]),
+// t, s. 64 bytes: p0 = {R00,R01,R02,R10}, p1 = {R11,R12,R20,R21},
+// p2 = {R22,t0,t1,t2}, p3 = {s0,s1,s2,0}.
+struct __align__(16) Pose {
+  float4 p0, p1, p2, p3;
+};
+
+// March transform of a primitive: voxel coordinate u = Mx * x + c, i.e. rows
+// {M_j0, M_j1, M_j2, c_j} with M = diag(h/s) R^T, c = h - M t, h = (M-1)/2.
+struct __align__(16) Xform {
+  float4 r0, r1, r2;
+};
+
+// BVH node: box plus children. Internal nodes 0..n-2, leaves n-1..2n-2.
+// Leaf: left = -1 - primitive id. Internal: left/right = child node indices.
+struct __align__(16) Node {
+  float lox, loy, loz;
+  int left;
+  float hix, hiy, hiz;
+  int right;
+};
+
+// Per-ray state saved by the forward for the adjoint (24 bytes).
+struct __align__(8) Saved {
+  float rho_r, rho_g, rho_b;  // c/a at the clamped sample
+  float beta;                 // (1 - T)/a at the clamped sample
+  int i_last;                 // last processed sample (-1: none)
+  int i_clamp;                // clamped sample or -1
+};
+
+// ---------------------------------------------------------------- spec math
+// Rotation from q/|q| with a fixed operation order (Sec. 3.1.2).
+__device__ __forceinline__ void rot_spec(float q0, float q1, float q2, float q3, float R[9]) {
+  float n2 = __fmul_rn(q0, q0);
+  n2 = __fadd_rn(n2, __fmul_rn(q1, q1));
+  n2 = __fadd_rn(n2, __fmul_rn(q2, q2));
+  n2 = __fadd_rn(n2, __fmul_rn(q3, q3));
+  float nrm = __fsqrt_rn(n2);
+  float w = __fdiv_rn(q0, nrm), x = __fdiv_rn(q1, nrm), y = __fdiv_rn(q2, nrm), z = __fdiv_rn(q3, nrm);
+  float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
+  float xy = __fmul_rn(x, y), xz = __fmul_rn(x, z), yz = __fmul_rn(y, z);
+  float wx = __fmul_rn(w, x), wy = __fmul_rn(w, y), wz = __fmul_rn(w, z);
+  R[0] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(yy, zz)));
+  R[1] = __fmul_rn(2.0f, __fsub_rn(xy, wz));
+  R[2] = __fmul_rn(2.0f, __fadd_rn(xz, wy));
+  R[3] = __fmul_rn(2.0f, __fadd_rn(xy, wz));
+  R[4] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, zz)));
+  R[5] = __fmul_rn(2.0f, __fsub_rn(yz, wx));
+  R[6] = __fmul_rn(2.0f, __fsub_rn(xz, wy));
+  R[7] = __fmul_rn(2.0f, __fadd_rn(yz, wx));
+  R[8] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, yy)));
+}
+
+// Slab interval of ray (o, d) against the box of a pose in its local frame
+// ([-1,1]^3), clipped to [t_near, t_far]. Fixed operation order; returns hit.
+__device__ __forceinline__ bool slab_spec(const Pose &P, float ox, float oy, float oz, float dx, float dy,
+                                          float dz, float t_near, float t_far, float &tin, float &tout) {
+  const float R[9] = {P.p0.x, P.p0.y, P.p0.z, P.p0.w, P.p1.x, P.p1.y, P.p1.z, P.p1.w, P.p2.x};
+  const float s[3] = {P.p3.x, P.p3.y, P.p3.z};
+  float p0 = __fsub_rn(ox, P.p2.y), p1 = __fsub_rn(oy, P.p2.z), p2 = __fsub_rn(oz, P.p2.w);
+  float lo = t_near, hi = t_far;
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    float on = __fmul_rn(R[0 * 3 + j], p0);
+    on = __fadd_rn(on, __fmul_rn(R[1 * 3 + j], p1));
+    on = __fadd_rn(on, __fmul_rn(R[2 * 3 + j], p2));
+    float dn = __fmul_rn(R[0 * 3 + j], dx);
+    dn = __fadd_rn(dn, __fmul_rn(R[1 * 3 + j], dy));
+    dn = __fadd_rn(dn, __fmul_rn(R[2 * 3 + j], dz));
+    float ol = __fdiv_rn(on, s[j]);
+    float dl = __fdiv_rn(dn, s[j]);
+    if (dl == 0.0f) {
+      if (ol < -1.0f || ol > 1.0f) ok = false;
+    } else {
+      float t1 = __fdiv_rn(__fsub_rn(-1.0f, ol), dl);
+      float t2 = __fdiv_rn(__fsub_rn(1.0f, ol), dl);
+      lo = fmaxf(lo, fminf(t1, t2));
+      hi = fminf(hi, fmaxf(t1, t2));
+    }
+  }
+  tin = lo;
+  tout = hi;
+  return ok && lo <= hi;
+}
+
+// Sample time t_i = t_near + i*dt (product rounded, then the sum).
+__device__ __forceinline__ float sample_t(float t_near, float dt, int i) {
+  return __fadd_rn(t_near, __fmul_rn((float)i, dt));
+}
+
+// Smallest i in [0, n] with t_i >= v (n if none). t_i is non-decreasing in i.
+__device__ __forceinline__ int first_sample_geq(float v, float t_near, float dt, int n) {
+  float x = (v - t_near) / dt;
+  int i;
+  if (!(x > 0.0f)) i = 0;
+  else if (x >= (float)n) i = n;
+  else i = (int)ceilf(x);
+  int it = 0;
+  while (i > 0 && sample_t(t_near, dt, i - 1) >= v && it < 64) { --i; ++it; }
+  while (i < n && sample_t(t_near, dt, i) < v && it < 128) { ++i; ++it; }
+  if (it >= 64) {  // estimate far off (huge t_near relative to dt): bisect
+    int lo = 0, hi = n;
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (sample_t(t_near, dt, mid) >= v) hi = mid; else lo = mid + 1;
+    }
+    i = lo;
+  }
+  return i;
+}
+
+// Smallest i in [0, n] with t_i > v (n if none).
+__device__ __forceinline__ int first_sample_gt(float v, float t_near, float dt, int n) {
+  float x = (v - t_near) / dt;
+  int i;
+  if (x < 0.0f) i = 0;
+  else if (x >= (float)n) i = n;
+  else i = (int)floorf(x) + 1;
+  int it = 0;
+  while (i > 0 && sample_t(t_near, dt, i - 1) > v && it < 64) { --i; ++it; }
+  while (i < n && sample_t(t_near, dt, i) <= v && it < 128) { ++i; ++it; }
+  if (it >= 64) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (sample_t(t_near, dt, mid) > v) hi = mid; else lo = mid + 1;
+    }
+    i = lo;
+  }
+  return i;
+}
+
+// ---------------------------------------------------------------- payload loads
+template <int DT>
+struct Voxel;
+
+template <>
+struct Voxel<MVP_F32> {
+  using T = float4;
+  __device__ __forceinline__ static float4 load(const void *base, int64_t v) {
+    return __ldg(reinterpret_cast<const float4 *>(base) + v);
+  }
+};
+
+template <>
+struct Voxel<MVP_BF16> {
+  __device__ __forceinline__ static float4 load(const void *base, int64_t v) {
+    uint2 r = __ldg(reinterpret_cast<const uint2 *>(base) + v);
+    float4 o;
+    o.x = __uint_as_float(r.x << 16);
+    o.y = __uint_as_float(r.x & 0xffff0000u);
+    o.z = __uint_as_float(r.y << 16);
+    o.w = __uint_as_float(r.y & 0xffff0000u);
+    return o;
+  }
+};
+
+template <>
+struct Voxel<MVP_F16> {
+  __device__ __forceinline__ static float4 load(const void *base, int64_t v) {
+    uint2 r = __ldg(reinterpret_cast<const uint2 *>(base) + v);
+    __half2 a = *reinterpret_cast<__half2 *>(&r.x);
+    __half2 b = *reinterpret_cast<__half2 *>(&r.y);
+    float2 fa = __half22float2(a), fb = __half22float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+  }
+};
+
+__device__ __forceinline__ float4 lerp4(float4 a, float4 b, float w) {
+  return make_float4(fmaf(w, b.x - a.x, a.x), fmaf(w, b.y - a.y, a.y), fmaf(w, b.z - a.z, a.z),
+                     fmaf(w, b.w - a.w, a.w));
+}
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(FULL, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+}  // namespace mvp

@@ -1,0 +1,319 @@
+// march.cu -- fused traversal + ray march + composite (Sec. 3.2.1, 3.2.2), the
+// evaluation-count variant, and per-ray hit-list export.
+//
+// One warp marches a tile of 32 neighbouring rays in lock step over the sample
+// index i (all rays share t_near and dt, so sample depths align). At each sample
+// the warp loops over the primitives active in the tile at that depth (the window
+// list built by build_window); each lane tests its own inclusive sample range for
+// the primitive and, if inside, gathers the 8 voxels of the cell, interpolates
+// RGBA and accumulates a = sum alpha, c = sum alpha*rgb. Then every lane applies
+// the clamped update w = min(a*dt, 1 - T). A tile stops when all its rays are done
+// (T >= 1 - eps_early). Empty depth ranges between primitives are skipped.
+#include "march.cuh"
+
+namespace mvp {
+
+template <int DT, int CAP, bool COUNT>
+__global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_march(MarchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  TileShared<CAP> &sh = reinterpret_cast<TileShared<CAP> *>(smem_raw)[warp];
+  const int64_t wt = (int64_t)blockIdx.x * TILE_WARPS + warp;
+  if (wt >= a.geom.n_warp_tiles) return;
+  LaneRay L;
+  load_lane_ray(L, a.o, a.d, tile_ray(a.geom, wt, lane));
+  const bool valid = L.r >= 0;
+  if (__ballot_sync(FULL, valid) == 0) return;
+
+  float T = 0.0f, Ir = 0.0f, Ig = 0.0f, Ib = 0.0f;
+  int i_last = a.n_steps - 1, i_clamp = -1;
+  float rho_r = 0.0f, rho_g = 0.0f, rho_b = 0.0f, beta = 0.0f;
+  int n_eval = 0;
+  bool alive = valid && a.n_steps > 0 && a.n_prims > 0;
+
+  Packet P;
+  make_packet(P, valid, L.o, L.d, a.t_far);
+  const int M = a.M, M2 = M * M;
+  const float Mm1 = (float)(M - 1);
+  const int64_t M3 = (int64_t)M2 * M;
+
+  int w0 = 0, wlen = a.n_steps;
+  while (w0 < a.n_steps && __any_sync(FULL, alive)) {
+    int w1 = min(a.n_steps, w0 + wlen);
+    int lane_last = alive ? a.n_steps - 1 : -1;
+    int ne = build_window<CAP>(sh, a.nodes, a.pose, a.xf, a.n_prims, P, L, lane_last, a.t_near, a.t_far, a.dt,
+                               a.n_steps, w0, w1);
+    if (ne < 0) {
+      if (w1 - w0 == 1) {  // one sample overlapped by more than CAP primitives
+        if (lane == 0) atomicOr(a.status, STATUS_CAPACITY);
+        alive = false;
+        break;
+      }
+      wlen = (w1 - w0 + 1) >> 1;
+      continue;
+    }
+    int i = w0;
+    while (i < w1) {
+      if (!__any_sync(FULL, alive)) break;
+      uint32_t m0, m1;
+      int nxt = active_set<CAP>(sh, ne, i, w1, m0, m1);
+      if ((m0 | m1) == 0) {
+        i = nxt;
+        continue;
+      }
+      for (; i < nxt; ++i) {
+        if (!__any_sync(FULL, alive)) break;
+        const float ti = sample_t(a.t_near, a.dt, i);
+        const float x0 = fmaf(ti, L.d[0], L.o[0]);
+        const float x1 = fmaf(ti, L.d[1], L.o[1]);
+        const float x2 = fmaf(ti, L.d[2], L.o[2]);
+        float sa = 0.0f, sr = 0.0f, sg = 0.0f, sb = 0.0f;
+        uint32_t b0 = m0, b1 = m1;
+        while (b0 | b1) {
+          int e;
+          if (b0) { e = __ffs(b0) - 1; b0 &= b0 - 1; }
+          else { e = 32 + __ffs(b1) - 1; b1 &= b1 - 1; }
+          const uint32_t rg = sh.erng[e][lane];
+          const bool in = alive && i >= (int)(rg & 0xffffu) && i <= (int)(rg >> 16);
+          if (in) {
+            const Xform X = sh.exf[e];
+            const int k = sh.ek[e];
+            float ux = fmaf(X.r0.x, x0, fmaf(X.r0.y, x1, fmaf(X.r0.z, x2, X.r0.w)));
+            float uy = fmaf(X.r1.x, x0, fmaf(X.r1.y, x1, fmaf(X.r1.z, x2, X.r1.w)));
+            float uz = fmaf(X.r2.x, x0, fmaf(X.r2.y, x1, fmaf(X.r2.z, x2, X.r2.w)));
+            ux = fminf(fmaxf(ux, 0.0f), Mm1);
+            uy = fminf(fmaxf(uy, 0.0f), Mm1);
+            uz = fminf(fmaxf(uz, 0.0f), Mm1);
+            const int ix = min((int)ux, M - 2), iy = min((int)uy, M - 2), iz = min((int)uz, M - 2);
+            const float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
+            const int64_t v = (int64_t)k * M3 + (int64_t)(iz * M2 + iy * M + ix);
+            const float4 c000 = Voxel<DT>::load(a.payload, v);
+            const float4 c001 = Voxel<DT>::load(a.payload, v + 1);
+            const float4 c010 = Voxel<DT>::load(a.payload, v + M);
+            const float4 c011 = Voxel<DT>::load(a.payload, v + M + 1);
+            const float4 c100 = Voxel<DT>::load(a.payload, v + M2);
+            const float4 c101 = Voxel<DT>::load(a.payload, v + M2 + 1);
+            const float4 c110 = Voxel<DT>::load(a.payload, v + M2 + M);
+            const float4 c111 = Voxel<DT>::load(a.payload, v + M2 + M + 1);
+            const float4 c00 = lerp4(c000, c001, fx), c01 = lerp4(c010, c011, fx);
+            const float4 c10 = lerp4(c100, c101, fx), c11 = lerp4(c110, c111, fx);
+            const float4 c0 = lerp4(c00, c01, fy), c1 = lerp4(c10, c11, fy);
+            const float4 val = lerp4(c0, c1, fz);
+            sa += val.w;
+            sr = fmaf(val.w, val.x, sr);
+            sg = fmaf(val.w, val.y, sg);
+            sb = fmaf(val.w, val.z, sb);
+            if (COUNT) ++n_eval;
+          }
+        }
+        if (alive) {
+          const float aa = sa * a.dt;
+          const float cr = sr * a.dt, cg = sg * a.dt, cb = sb * a.dt;
+          const float rem = 1.0f - T;
+          if (aa <= rem) {
+            Ir += cr;
+            Ig += cg;
+            Ib += cb;
+            T = fminf(T + aa, 1.0f);
+          } else {
+            const float bt = rem / aa;
+            Ir = fmaf(cr, bt, Ir);
+            Ig = fmaf(cg, bt, Ig);
+            Ib = fmaf(cb, bt, Ib);
+            i_clamp = i;
+            rho_r = cr / aa;
+            rho_g = cg / aa;
+            rho_b = cb / aa;
+            beta = bt;
+            T = 1.0f;
+          }
+          if (T >= a.stop_T) {
+            alive = false;
+            i_last = i;
+          }
+        }
+      }
+    }
+    w0 = w1;
+    wlen = min(a.n_steps, wlen * 2);
+  }
+  if (!valid) return;
+  if (COUNT) {
+    a.n_eval[L.r] = n_eval;
+    return;
+  }
+  const float bgw = 1.0f - T;
+  float4 out = make_float4(fmaf(bgw, a.bg[0], Ir), fmaf(bgw, a.bg[1], Ig), fmaf(bgw, a.bg[2], Ib), T);
+  reinterpret_cast<float4 *>(a.out)[L.r] = out;
+  if (a.saved) {
+    Saved S;
+    S.rho_r = rho_r;
+    S.rho_g = rho_g;
+    S.rho_b = rho_b;
+    S.beta = beta;
+    S.i_last = i_last;
+    S.i_clamp = i_clamp;
+    a.saved[L.r] = S;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Hit lists: each lane emits its ray's (primitive, tin, tout). Passes over the
+// depth range in windows; a hit belongs to the window that holds its tin, so a
+// window split after an overflow never emits a hit twice. FILL = false counts.
+template <bool FILL>
+__global__ void __launch_bounds__(TILE_WARPS * 32) k_hits(HitArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  TileShared<1> &sh = reinterpret_cast<TileShared<1> *>(smem_raw)[warp];
+  const int64_t wt = (int64_t)blockIdx.x * TILE_WARPS + warp;
+  if (wt >= a.geom.n_warp_tiles) return;
+  LaneRay L;
+  load_lane_ray(L, a.o, a.d, tile_ray(a.geom, wt, lane));
+  const bool valid = L.r >= 0;
+  if (__ballot_sync(FULL, valid) == 0) return;
+  Packet P;
+  make_packet(P, valid, L.o, L.d, a.t_far);
+  int64_t count = 0;
+  const int64_t base = (FILL && valid) ? a.offs[L.r] : 0;
+  float ta = a.t_near, span = a.t_far - a.t_near;
+  int guard = 0;
+  while (ta <= a.t_far && guard < 4096) {
+    ++guard;
+    float tb = fminf(ta + span, a.t_far);
+    bool last = tb >= a.t_far;
+    int64_t c0 = count;
+    auto emit = [&](int nc) -> bool {
+      for (int c = 0; c < nc; ++c) {
+        int k = sh.cand[c];
+        if (!valid) continue;
+        const float4 *pp = reinterpret_cast<const float4 *>(a.pose + k);
+        Pose Pk;
+        Pk.p0 = __ldg(pp);
+        Pk.p1 = __ldg(pp + 1);
+        Pk.p2 = __ldg(pp + 2);
+        Pk.p3 = __ldg(pp + 3);
+        float tin, tout;
+        if (slab_spec(Pk, L.o[0], L.o[1], L.o[2], L.d[0], L.d[1], L.d[2], a.t_near, a.t_far, tin, tout) &&
+            tin >= ta && (last ? tin <= tb : tin < tb)) {
+          if (FILL) {
+            int64_t w = base + count;
+            if (w < a.cap) {
+              a.ids[w] = k;
+              a.tin[w] = tin;
+              a.tout[w] = tout;
+            }
+          }
+          ++count;
+        }
+      }
+      return true;
+    };
+    float slack = 1.0e-5f * (fabsf(ta) + fabsf(tb)) + 1.0e-30f;
+    bool ok = traverse_tile(sh, a.nodes, a.n_prims, P, ta - slack, tb + slack, emit);
+    __syncwarp();
+    if (!ok) {
+      count = c0;  // drop this window's partial output and retry a narrower one
+      span *= 0.5f;
+      if (!(span > 1.0e-6f * (fabsf(ta) + 1.0f))) {
+        if (lane == 0) atomicOr(a.status, STATUS_CAPACITY);
+        break;
+      }
+      continue;
+    }
+    if (last) break;
+    ta = tb;
+    span = fminf(span * 2.0f, a.t_far - a.t_near);
+  }
+  if (!FILL && valid) a.counts[L.r] = count;
+}
+
+// Inclusive prefix sum of counts into offs[1..n], offs[0] = 0 (single block).
+__global__ void __launch_bounds__(1024) k_offsets(const int64_t *__restrict__ counts, int64_t n,
+                                                  int64_t *__restrict__ offs) {
+  __shared__ int64_t wsum[32];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t base = 0; base < n; base += blockDim.x) {
+    int64_t i = base + threadIdx.x;
+    int64_t v = i < n ? counts[i] : 0;
+    int64_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t u = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      int64_t w = wsum[lane];
+      int64_t iw = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int64_t u = __shfl_up_sync(FULL, iw, o);
+        if (lane >= o) iw += u;
+      }
+      wsum[lane] = iw - w;
+    }
+    __syncthreads();
+    if (i < n) offs[i + 1] = carry + wsum[warp] + incl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += wsum[warp] + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) offs[0] = 0;
+}
+
+// ----------------------------------------------------------------------------
+template <int DT, int CAP, bool COUNT>
+static cudaError_t launch_march_t(const MarchArgs &a, cudaStream_t st) {
+  size_t smem = sizeof(TileShared<CAP>) * TILE_WARPS;
+  static bool attr_set = false;  // per instantiation; set once per process
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_march<DT, CAP, COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int64_t blocks = (a.geom.n_warp_tiles + TILE_WARPS - 1) / TILE_WARPS;
+  if (blocks == 0) return cudaSuccess;
+  k_march<DT, CAP, COUNT><<<(unsigned)blocks, TILE_WARPS * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool COUNT>
+static cudaError_t launch_march_c(const MarchArgs &a, cudaStream_t st) {
+  switch (a.dtype) {
+    case MVP_F32: return launch_march_t<MVP_F32, MARCH_CAP, COUNT>(a, st);
+    case MVP_BF16: return launch_march_t<MVP_BF16, MARCH_CAP, COUNT>(a, st);
+    case MVP_F16: return launch_march_t<MVP_F16, MARCH_CAP, COUNT>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_march(const MarchArgs &a, cudaStream_t st) {
+  return a.n_eval ? launch_march_c<true>(a, st) : launch_march_c<false>(a, st);
+}
+
+cudaError_t launch_hits(const HitArgs &a, int64_t *counts, cudaStream_t st) {
+  int64_t blocks = (a.geom.n_warp_tiles + TILE_WARPS - 1) / TILE_WARPS;
+  size_t smem = sizeof(TileShared<1>) * TILE_WARPS;
+  if (blocks > 0) {
+    HitArgs c = a;
+    c.counts = counts;
+    k_hits<false><<<(unsigned)blocks, TILE_WARPS * 32, smem, st>>>(c);
+  }
+  k_offsets<<<1, 1024, 0, st>>>(counts, a.geom.n_rays, a.offs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hits_fill(const HitArgs &a, cudaStream_t st) {
+  int64_t blocks = (a.geom.n_warp_tiles + TILE_WARPS - 1) / TILE_WARPS;
+  size_t smem = sizeof(TileShared<1>) * TILE_WARPS;
+  if (blocks > 0) k_hits<true><<<(unsigned)blocks, TILE_WARPS * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace mvp

@@ -1,0 +1,60 @@
+// march.cuh -- launch arguments of the march, hit-list and adjoint kernels.
+#pragma once
+
+#include "tile.cuh"
+
+namespace mvp {
+
+constexpr int MARCH_CAP = 64;  // primitives a warp tile holds per depth window
+
+struct MarchArgs {
+  // primitives and their BVH
+  int n_prims, M, dtype;
+  const void *payload;
+  const Node *nodes;
+  const Pose *pose;
+  const Xform *xf;
+  // rays
+  TileGeom geom;
+  const float *o, *d;
+  float t_near, t_far, dt, stop_T;
+  float bg[3];
+  int n_steps;
+  // outputs
+  float *out;
+  Saved *saved;
+  int32_t *n_eval;  // count variant when non-null
+  int *status;
+};
+
+struct HitArgs {
+  int n_prims;
+  const Node *nodes;
+  const Pose *pose;
+  TileGeom geom;
+  const float *o, *d;
+  float t_near, t_far;
+  int64_t *counts;       // count pass
+  const int64_t *offs_in;
+  int64_t *offs;
+  int32_t *ids;
+  float *tin, *tout;
+  int64_t cap;
+  int *status;
+};
+
+struct BwdArgs {
+  MarchArgs m;             // geometry, rays, payload (out/saved/n_eval unused)
+  const Saved *saved;
+  const float *grad;       // [n][4]
+  float *g_payload;        // [n][M^3][4] or null
+  float *gmc;              // [n][12] accumulators or null
+};
+
+cudaError_t launch_march(const MarchArgs &a, cudaStream_t st);
+cudaError_t launch_hits(const HitArgs &a, int64_t *counts, cudaStream_t st);
+cudaError_t launch_hits_fill(const HitArgs &a, cudaStream_t st);
+cudaError_t launch_backward(const BwdArgs &a, const float *t, const float *q, const float *s, float *g_t,
+                            float *g_q, float *g_s, cudaStream_t st);
+
+}  // namespace mvp

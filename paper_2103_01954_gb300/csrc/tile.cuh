@@ -1,0 +1,290 @@
+// tile.cuh -- warp-level tile machinery shared by the march, hit-list and adjoint
+// kernels: ray tiles, the interval ray packet, the BVH traversal of a tile, and
+// the per-window primitive list with per-lane sample ranges.
+//
+// A warp owns a tile of 32 rays (8x4 pixels for image rays, else 32 consecutive
+// rays). It traverses the BVH once for the whole tile with an interval-arithmetic
+// slab test of the tile's ray packet (origins and directions bounded per axis),
+// 32 nodes per step, and collects candidate leaves. Each candidate is then tested
+// against every lane's ray with the exact FP32 slab test (Sec. 3.2.1: the list of
+// primitives each ray intersects), and kept if any lane hits it; the lane's hit
+// interval becomes an inclusive sample-index range [i_lo, i_hi] (packed 16+16 bits).
+#pragma once
+
+#include "bvh.cuh"
+
+namespace mvp {
+
+constexpr int TILE_WARPS = 4;  // warps per block; a block covers 16x8 pixels
+constexpr int STACK = 256;     // traversal stack entries per warp
+constexpr int CBUF = 64;       // candidate leaves buffered per warp
+constexpr uint32_t EMPTY_RANGE = 0x0000ffffu;  // i_lo = 65535 > i_hi = 0
+
+struct TileGeom {
+  int64_t n_rays;
+  int width, height;  // > 0: 2-D image tiles
+  int64_t n_warp_tiles;
+};
+
+__host__ __device__ inline TileGeom make_tile_geom(int64_t n_rays, int width, int height) {
+  TileGeom g;
+  g.n_rays = n_rays;
+  bool img = width > 0 && height > 0 && (int64_t)width * height == n_rays;
+  g.width = img ? width : 0;
+  g.height = img ? height : 0;
+  if (img)
+    g.n_warp_tiles = (int64_t)((width + 15) / 16) * ((height + 7) / 8) * 4;
+  else
+    g.n_warp_tiles = ((n_rays + 31) / 32 + 3) / 4 * 4;
+  return g;
+}
+
+// Ray index of `lane` in warp tile `wt`, or -1.
+__device__ __forceinline__ int64_t tile_ray(const TileGeom &g, int64_t wt, int lane) {
+  if (g.width > 0) {
+    int64_t bt = wt >> 2;
+    int w = (int)(wt & 3);
+    int stx = (g.width + 15) / 16;
+    int64_t sy = bt / stx, sx = bt - sy * stx;
+    int64_t px = sx * 16 + (w & 1) * 8 + (lane & 7);
+    int64_t py = sy * 8 + (w >> 1) * 4 + (lane >> 3);
+    if (px >= g.width || py >= g.height) return -1;
+    return py * g.width + px;
+  }
+  int64_t r = wt * 32 + lane;
+  return r < g.n_rays ? r : -1;
+}
+
+// Interval bounds of the tile's rays.
+struct Packet {
+  float omin[3], omax[3];
+  float dmin[3], dmax[3];
+  float inv_lo[3], inv_hi[3];  // 1/|d| bounds on axes where d keeps one sign
+  int sgn[3];                  // +1, -1, or 0 (directions straddle zero)
+  float margin;                // world-space slack for rounding
+};
+
+__device__ __forceinline__ void make_packet(Packet &P, bool valid, const float o[3], const float d[3], float t_far) {
+  float om = 0.0f, dm = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    P.omin[j] = warp_min(valid ? o[j] : INFINITY);
+    P.omax[j] = warp_max(valid ? o[j] : -INFINITY);
+    P.dmin[j] = warp_min(valid ? d[j] : INFINITY);
+    P.dmax[j] = warp_max(valid ? d[j] : -INFINITY);
+    om = fmaxf(om, fmaxf(fabsf(P.omin[j]), fabsf(P.omax[j])));
+    dm = fmaxf(dm, fmaxf(fabsf(P.dmin[j]), fabsf(P.dmax[j])));
+    if (P.dmin[j] > 0.0f) {
+      P.sgn[j] = 1;
+      P.inv_lo[j] = 1.0f / P.dmax[j];  // smallest 1/|d|
+      P.inv_hi[j] = 1.0f / P.dmin[j];  // largest 1/|d|
+    } else if (P.dmax[j] < 0.0f) {
+      P.sgn[j] = -1;
+      P.inv_lo[j] = 1.0f / -P.dmin[j];
+      P.inv_hi[j] = 1.0f / -P.dmax[j];
+    } else {
+      P.sgn[j] = 0;
+      P.inv_lo[j] = P.inv_hi[j] = 0.0f;
+    }
+  }
+  P.margin = 1.0e-5f * (om + fabsf(t_far) * dm) + 1.0e-30f;
+}
+
+// Can some ray of the packet meet the (inflated) box for t in [ta, tb]?
+// Conservative: every bound is widened by the packet margin plus 1e-5 relative.
+__device__ __forceinline__ bool packet_hits_box(const Packet &P, float4 a, float4 b, float ta, float tb) {
+  const float lo[3] = {a.x, a.y, a.z}, hi[3] = {b.x, b.y, b.z};
+  float tmin = ta, tmax = tb;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    float m = P.margin + 1.0e-5f * fmaxf(fabsf(lo[j]), fabsf(hi[j]));
+    float l = lo[j] - m, h = hi[j] + m;
+    if (P.sgn[j] > 0) {
+      // entry (l - o)/d: smallest over the packet; exit (h - o)/d: largest
+      float n1 = l - P.omax[j];
+      float te = n1 * (n1 >= 0.0f ? P.inv_lo[j] : P.inv_hi[j]);
+      float n2 = h - P.omin[j];
+      float tx = n2 * (n2 >= 0.0f ? P.inv_hi[j] : P.inv_lo[j]);
+      tmin = fmaxf(tmin, te);
+      tmax = fminf(tmax, tx);
+    } else if (P.sgn[j] < 0) {
+      // entry (o - h)/|d|, exit (o - l)/|d|
+      float n1 = P.omin[j] - h;
+      float te = n1 * (n1 >= 0.0f ? P.inv_lo[j] : P.inv_hi[j]);
+      float n2 = P.omax[j] - l;
+      float tx = n2 * (n2 >= 0.0f ? P.inv_hi[j] : P.inv_lo[j]);
+      tmin = fmaxf(tmin, te);
+      tmax = fminf(tmax, tx);
+    }
+    // sgn == 0: a ray parallel to the slab may lie inside it for every t
+  }
+  return tmin <= tmax + 1.0e-5f * (fabsf(tmax) + fabsf(tmin)) + 1.0e-30f;
+}
+
+// Warp-private shared memory of a tile.
+template <int CAP>
+struct TileShared {
+  int stack[STACK];
+  int cand[CBUF];
+  Xform exf[CAP];
+  int ek[CAP];
+  int elo[CAP], ehi[CAP];
+  uint32_t erng[CAP][32];
+};
+
+// Traverse the BVH for the packet over [ta, tb]. Candidate leaves (primitive ids)
+// are passed to `emit(nc)` in batches of up to CBUF via sh.cand; emit returns false
+// to abort. Returns false on stack overflow or an aborted emit.
+template <class SH, class Emit>
+__device__ __forceinline__ bool traverse_tile(SH &sh, const Node *__restrict__ nodes, int n_prims,
+                                              const Packet &P, float ta, float tb, Emit &&emit) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  if (n_prims <= 0) return true;
+  if (lane == 0) sh.stack[0] = 0;  // root: internal node 0, or leaf 0 when n == 1
+  __syncwarp();
+  int sp = 1, nc = 0;
+  while (true) {
+    if (sp > 0 && nc < 32) {
+      int take = sp < 32 ? sp : 32;
+      sp -= take;
+      int node = lane < take ? sh.stack[sp + lane] : -1;
+      __syncwarp();
+      bool pass = false, leaf = false;
+      int l = 0, r = 0;
+      if (node >= 0) {
+        const float4 *np = reinterpret_cast<const float4 *>(nodes + node);
+        float4 a = __ldg(np), b = __ldg(np + 1);
+        l = __float_as_int(a.w);
+        r = __float_as_int(b.w);
+        leaf = l < 0;
+        pass = packet_hits_box(P, a, b, ta, tb);
+      }
+      unsigned mleaf = __ballot_sync(FULL, pass && leaf);
+      unsigned minner = __ballot_sync(FULL, pass && !leaf);
+      int nl = __popc(mleaf), ni = __popc(minner);
+      if (sp + 2 * ni > STACK) return false;
+      if (pass && leaf) sh.cand[nc + __popc(mleaf & lt)] = -1 - l;
+      if (pass && !leaf) {
+        int pos = sp + 2 * __popc(minner & lt);
+        sh.stack[pos] = r;
+        sh.stack[pos + 1] = l;
+      }
+      sp += 2 * ni;
+      nc += nl;
+      __syncwarp();
+    } else {
+      if (nc == 0) break;
+      if (!emit(nc)) return false;
+      nc = 0;
+      __syncwarp();
+    }
+  }
+  return true;
+}
+
+// Per-lane ray data of a tile.
+struct LaneRay {
+  int64_t r;  // ray index or -1
+  float o[3], d[3];
+};
+
+__device__ __forceinline__ void load_lane_ray(LaneRay &L, const float *__restrict__ o, const float *__restrict__ d,
+                                              int64_t r) {
+  L.r = r;
+  if (r >= 0) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      L.o[j] = o[3 * r + j];
+      L.d[j] = d[3 * r + j];
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) L.o[j] = L.d[j] = 0.0f;
+  }
+}
+
+// Build the window's primitive list for samples [w0, w1): every traversal
+// candidate that some lane's exact slab interval meets at a sample of the window
+// with index <= lane_last (the lane's last live sample). Returns the number of
+// entries, or -1 if more than CAP are needed or the traversal stack overflowed.
+template <int CAP>
+__device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__restrict__ nodes,
+                                            const Pose *__restrict__ pose, const Xform *__restrict__ xf,
+                                            int n_prims, const Packet &P, const LaneRay &L, int lane_last,
+                                            float t_near, float t_far, float dt, int n_steps, int w0, int w1) {
+  const int lane = threadIdx.x & 31;
+  float ta = sample_t(t_near, dt, w0);
+  float tb = sample_t(t_near, dt, w1 - 1);
+  int ne = 0;
+  bool live = L.r >= 0 && lane_last >= w0;
+  int hi_cap = min(w1 - 1, lane_last);
+  auto emit = [&](int nc) -> bool {
+    for (int c = 0; c < nc; ++c) {
+      int k = sh.cand[c];
+      const float4 *pp = reinterpret_cast<const float4 *>(pose + k);
+      Pose Pk;
+      Pk.p0 = __ldg(pp);
+      Pk.p1 = __ldg(pp + 1);
+      Pk.p2 = __ldg(pp + 2);
+      Pk.p3 = __ldg(pp + 3);
+      int ilo = 1, ihi = 0;
+      if (live) {
+        float tin, tout;
+        if (slab_spec(Pk, L.o[0], L.o[1], L.o[2], L.d[0], L.d[1], L.d[2], t_near, t_far, tin, tout)) {
+          ilo = max(first_sample_geq(tin, t_near, dt, n_steps), w0);
+          ihi = min(first_sample_gt(tout, t_near, dt, n_steps) - 1, hi_cap);
+        }
+      }
+      bool has = ilo <= ihi;
+      if (__ballot_sync(FULL, has) == 0) continue;
+      if (ne >= CAP) return false;
+      int lo_min = __reduce_min_sync(FULL, has ? ilo : 0x7fffffff);
+      int hi_max = __reduce_max_sync(FULL, has ? ihi : -1);
+      sh.erng[ne][lane] = has ? ((uint32_t)ilo | ((uint32_t)ihi << 16)) : EMPTY_RANGE;
+      if (lane == 0) {
+        sh.ek[ne] = k;
+        sh.elo[ne] = lo_min;
+        sh.ehi[ne] = hi_max;
+        const float4 *xp = reinterpret_cast<const float4 *>(xf + k);
+        sh.exf[ne].r0 = __ldg(xp);
+        sh.exf[ne].r1 = __ldg(xp + 1);
+        sh.exf[ne].r2 = __ldg(xp + 2);
+      }
+      ++ne;
+    }
+    return true;
+  };
+  // the packet test uses the window's time range with a small slack
+  float slack = 1.0e-5f * (fabsf(ta) + fabsf(tb)) + 1.0e-30f;
+  bool ok = traverse_tile(sh, nodes, n_prims, P, ta - slack, tb + slack, emit);
+  __syncwarp();
+  return ok ? ne : -1;
+}
+
+// Active entries at sample i (two 32-bit masks) and the next sample at which the
+// active set changes (capped at w1).
+template <int CAP>
+__device__ __forceinline__ int active_set(const TileShared<CAP> &sh, int ne, int i, int w1, uint32_t &m0,
+                                          uint32_t &m1) {
+  const int lane = threadIdx.x & 31;
+  int nxt = 0x7fffffff;
+  bool a0 = false, a1 = false;
+  if (lane < ne) {
+    int lo = sh.elo[lane], hi = sh.ehi[lane];
+    a0 = lo <= i && i <= hi;
+    nxt = lo > i ? lo : (hi >= i ? hi + 1 : 0x7fffffff);
+  }
+  if (CAP > 32 && lane + 32 < ne) {
+    int lo = sh.elo[lane + 32], hi = sh.ehi[lane + 32];
+    a1 = lo <= i && i <= hi;
+    int v = lo > i ? lo : (hi >= i ? hi + 1 : 0x7fffffff);
+    nxt = min(nxt, v);
+  }
+  m0 = __ballot_sync(FULL, a0);
+  m1 = __ballot_sync(FULL, a1);
+  nxt = __reduce_min_sync(FULL, nxt);
+  return min(nxt, w1);
+}
+
+}  // namespace mvp

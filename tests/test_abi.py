@@ -1,0 +1,76 @@
+"""The C ABI library builds, loads and exports every function include/mvp.h
+declares; host-only calls (no GPU needed) behave as documented."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2103_01954_gb300 import binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    hdr = open(os.path.join(ROOT, "include", "mvp.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(mvp_\w+)\s*\(", hdr, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("mvp_build_bvh", "mvp_raymarch_fwd", "mvp_raymarch_bwd", "mvp_hitlists",
+                     "mvp_ctx_create", "mvp_pack_payload"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    path = B.library_path()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (mvp_\w+)$", out, flags=re.M))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    L = B.lib()
+    for n in declared_functions():
+        assert getattr(L, n) is not None
+    # the binding declares a signature for every symbol
+    assert set(n for n, _, _ in B._SIGS) == set(declared_functions())
+
+
+def test_host_only_calls():
+    L = B.lib()
+    assert b"sm_103a" in L.mvp_version()
+    assert L.mvp_status_string(B.MVP_ERR_CAPACITY) == b"MVP_ERR_CAPACITY"
+    assert L.mvp_num_steps(1.0, 5.0, 0.01) == 400
+    assert L.mvp_num_steps(1.0, 5.0, 0.005) == 800
+    assert L.mvp_num_steps(1.0, 1.0, 0.01) == 0
+    assert L.mvp_saved_bytes(10) == 240
+    assert L.mvp_saved_bytes(0) == 0
+
+
+def test_num_steps_matches_input_generator():
+    import synthetic
+    for t0, t1, dt in [(1.0, 5.0, 0.01), (1.0, 5.0, 0.005), (0.5, 2.25, 0.0025), (0.0, 6.0, 0.01), (2.0, 2.0005, 1e-3)]:
+        r = synthetic.Rays(o=None, d=None, t_near=t0, t_far=t1, dt=dt)
+        assert B.lib().mvp_num_steps(t0, t1, dt) == r.n_steps
+
+
+def test_ctx_create_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    st = B.lib().mvp_ctx_create(0, ctypes.byref(h))
+    assert st in (B.MVP_ERR_CUDA, B.MVP_ERR_INVALID_ARG)
+    assert B.lib().mvp_last_error() != b""
+    with pytest.raises(B.MVPError):
+        B.check(st, "ctx")
+
+
+def test_invalid_arguments_rejected_on_host():
+    # a NULL context is rejected before anything touches the device
+    L = B.lib()
+    pr = B.mvp_prims(n=1, M=1, dtype=0)
+    assert L.mvp_build_bvh(None, ctypes.byref(pr), None, None) == B.MVP_ERR_INVALID_ARG
+    assert L.mvp_raymarch_fwd(None, ctypes.byref(pr), None, None, None, None, None) == B.MVP_ERR_INVALID_ARG

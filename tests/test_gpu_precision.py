@@ -1,0 +1,84 @@
+"""Reduced-precision payloads (BF16, FP16; interpolation and compositing stay FP32).
+
+The conversion kernel is byte work: bit-exact against PyTorch's CPU round-to-nearest
+conversion. The march on a converted payload is held to the FP32 parity bar against
+the oracle run on the same (dequantised, exactly representable) values; the error
+against the oracle on the original FP32 payload is reported per dtype.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+from helpers import rays_from
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from gpu_util import DEV, Dev, image_parity  # noqa: E402
+from paper_2103_01954_gb300 import torch_ops as T  # noqa: E402
+
+F32M = oracle.MODE_PRUNED | oracle.MEMBER_F32
+DTYPES = [torch.bfloat16, torch.float16]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_pack_bit_exact(dtype):
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(4 * 1000 + 3).astype(np.float32) * 10  # ragged tail
+    x[:8] = [0.0, -0.0, 1e-30, 65504.0, 1e5, -3.0e38, 1.0 + 2 ** -9, 1.0 + 3 * 2 ** -9]
+    ctx = T.Context(0)
+    g = T.pack_payload(ctx, torch.from_numpy(x).to(DEV), dtype)
+    ref = torch.from_numpy(x).to(dtype)
+    torch.cuda.synchronize()
+    assert torch.equal(g.cpu().view(torch.int16), ref.view(torch.int16))
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("cfg", ["small_512x8^3_96x128", "small_4096x16^3_83x128"])
+def test_reduced_precision_payload(dtype, cfg):
+    sc, rays, _ = synthetic.make_config(cfg, 0)
+    dv = Dev(sc, rays, payload_dtype=dtype).build()
+    out, _ = dv.render()
+    o = out.cpu().numpy()
+    deq = torch.from_numpy(sc.payload).to(dtype).float().numpy()
+    sc_q = synthetic.Scene(t=sc.t, q=sc.q, s=sc.s, payload=deq, M=sc.M)
+    ref_q = oracle.render(sc_q, rays, F32M)["rgba"]
+    st = image_parity(o, ref_q)
+    assert st["frac_2e-4"] >= 0.999 and st["max"] <= 1e-2, st
+    ref32 = oracle.render(sc, rays, F32M)["rgba"]
+    e = np.abs(o - ref32)
+    print(f"{cfg} {dtype}: vs FP32-payload oracle max {e.max():.3e} p99.9 {np.quantile(e, 0.999):.3e}; "
+          f"vs dequantised oracle max {st['max']:.3e}")
+    assert e.max() < 0.1
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_reduced_precision_paper_scale_sampled(dtype):
+    sc, rays, _ = synthetic.make_config("paper_4096x16^3_667x1024", 0)
+    dv = Dev(sc, rays, payload_dtype=dtype).build()
+    out, _ = dv.render()
+    sel = np.random.default_rng(2).choice(rays.n, 2000, replace=False)
+    sub = rays_from(rays.o[sel], rays.d[sel], rays.t_near, rays.t_far, rays.dt)
+    deq = torch.from_numpy(sc.payload).to(dtype).float().numpy()
+    ref_q = oracle.render(synthetic.Scene(t=sc.t, q=sc.q, s=sc.s, payload=deq, M=sc.M), sub, F32M)["rgba"]
+    st = image_parity(out.cpu().numpy()[sel], ref_q)
+    assert st["frac_2e-4"] >= 0.999 and st["max"] <= 1e-2, st
+
+
+def test_bf16_backward_runs_and_matches_dequantised_oracle():
+    sc, rays, _ = synthetic.make_config("diff_small_64x8^3_2x48x40", 0)
+    dv = Dev(sc, rays, payload_dtype=torch.bfloat16).build()
+    out, saved = T.raymarch_fwd(dv.ctx, dv.prims, dv.bvh, dv.rs, want_saved=True)
+    g = np.random.default_rng(0).standard_normal((rays.n, 4)).astype(np.float32)
+    gp = torch.zeros(dv.payload.shape, dtype=torch.float32, device=DEV)
+    T.raymarch_bwd(dv.ctx, dv.prims, dv.bvh, dv.rs, saved, torch.from_numpy(g).to(DEV), gp)
+    dv.ctx.sync()
+    deq = torch.from_numpy(sc.payload).to(torch.bfloat16).float().numpy()
+    R = oracle.backward(synthetic.Scene(t=sc.t, q=sc.q, s=sc.s, payload=deq, M=sc.M), rays,
+                        g.astype(np.float64), F32M)
+    ref = R["g_payload"]
+    assert np.abs(gp.cpu().numpy() - ref).max() / np.abs(ref).max() <= 1e-3
