@@ -99,25 +99,27 @@ void orc_rotations_f32spec(int n, const float *q, float *R_out) {
 /* Slab method in the primitive's local frame, where the box is [-1,1]^3.      */
 /* ------------------------------------------------------------------------- */
 
-/* FP32 decision, fixed operation order. Returns 1 on a hit with [tin, tout]. */
+/* FP32 decision, fixed operation order, each step correctly rounded (fmaf is the
+ * fused multiply-add with one rounding): p = o - t; per axis j
+ * ol = fma(R2j, p2, fma(R1j, p1, R0j*p0)) * (1/s_j), dl likewise with d; a ray with
+ * dl == 0 is inside the slab iff |ol| <= 1, else with r = 1/dl the slab spans
+ * (-1 - ol)*r .. (1 - ol)*r. Returns 1 on a hit with [tin, tout]. */
 static int slab_f32spec(const float R[9], const float *t, const float *s, const float *o,
                         const float *d, float t_near, float t_far, float *tin, float *tout) {
   float p0 = o[0] - t[0], p1 = o[1] - t[1], p2 = o[2] - t[2];
   float lo = t_near, hi = t_far;
   for (int j = 0; j < 3; ++j) {
-    float on = R[0 * 3 + j] * p0;
-    on = on + R[1 * 3 + j] * p1;
-    on = on + R[2 * 3 + j] * p2;
-    float dn = R[0 * 3 + j] * d[0];
-    dn = dn + R[1 * 3 + j] * d[1];
-    dn = dn + R[2 * 3 + j] * d[2];
-    float ol = on / s[j];
-    float dl = dn / s[j];
+    float is = 1.0f / s[j];
+    float on = fmaf(R[2 * 3 + j], p2, fmaf(R[1 * 3 + j], p1, R[0 * 3 + j] * p0));
+    float dn = fmaf(R[2 * 3 + j], d[2], fmaf(R[1 * 3 + j], d[1], R[0 * 3 + j] * d[0]));
+    float ol = on * is;
+    float dl = dn * is;
     if (dl == 0.0f) {
       if (ol < -1.0f || ol > 1.0f) return 0;
     } else {
-      float t1 = (-1.0f - ol) / dl;
-      float t2 = (1.0f - ol) / dl;
+      float r = 1.0f / dl;
+      float t1 = (-1.0f - ol) * r;
+      float t2 = (1.0f - ol) * r;
       lo = fmaxf(lo, fminf(t1, t2));
       hi = fminf(hi, fmaxf(t1, t2));
     }

@@ -18,7 +18,7 @@
 
 namespace mvp {
 
-template <int DT, int CAP>
+template <int DT, int CAP, int MT>
 __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const MarchArgs &a = b.m;
@@ -55,18 +55,18 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
     }
   }
   if (a.n_prims <= 0 || a.n_steps <= 0) return;
-  Packet P;
-  make_packet(P, valid, L.o, L.d, a.t_far);
-  const int M = a.M, M2 = M * M;
+  make_packet(sh.pk, valid, L.o, L.d, a.t_far);
+  const int M = MT > 0 ? MT : a.M, M2 = M * M;
   const float Mm1 = (float)(M - 1);
-  const int64_t M3 = (int64_t)M2 * M;
+  constexpr int VB = DT == MVP_F32 ? 16 : 8;
+  const int64_t prim_bytes = (int64_t)M2 * M * VB;
   const int max_last = __reduce_max_sync(FULL, i_last);
 
   int w0 = 0, wlen = a.n_steps;
   while (w0 <= max_last) {
     int w1 = min(a.n_steps, w0 + wlen);
-    int ne = build_window<CAP>(sh, a.nodes, a.pose, a.xf, a.n_prims, P, L, valid ? i_last : -1, a.t_near,
-                               a.t_far, a.dt, a.n_steps, w0, w1);
+    int ne = build_window<CAP>(sh, a.nodes, a.pose, a.xf, reinterpret_cast<const char *>(a.payload), prim_bytes,
+                               a.n_prims, L, valid ? i_last : -1, a.t_near, a.t_far, a.dt, a.n_steps, w0, w1);
     if (ne < 0) {
       if (w1 - w0 == 1) {
         if (lane == 0) atomicOr(a.status, STATUS_CAPACITY);
@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
     for (int e = 0; e < ne; ++e) {
       const int k = sh.ek[e];
       const Xform X = sh.exf[e];
+      const void *pbase = sh.eptr[e];
       const uint32_t rg = sh.erng[e][lane];
       const int lo = (int)(rg & 0xffffu), hi = (int)(rg >> 16);
       const float4 tk = __ldg(reinterpret_cast<const float4 *>(a.pose + k) + 2);  // {R22, t0, t1, t2}
@@ -100,15 +101,16 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
         uz = fminf(fmaxf(uz, 0.0f), Mm1);
         const int ix = min((int)ux, M - 2), iy = min((int)uy, M - 2), iz = min((int)uz, M - 2);
         const float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
-        const int64_t v = (int64_t)k * M3 + (int64_t)(iz * M2 + iy * M + ix);
-        const float4 c000 = Voxel<DT>::load(a.payload, v);
-        const float4 c001 = Voxel<DT>::load(a.payload, v + 1);
-        const float4 c010 = Voxel<DT>::load(a.payload, v + M);
-        const float4 c011 = Voxel<DT>::load(a.payload, v + M + 1);
-        const float4 c100 = Voxel<DT>::load(a.payload, v + M2);
-        const float4 c101 = Voxel<DT>::load(a.payload, v + M2 + 1);
-        const float4 c110 = Voxel<DT>::load(a.payload, v + M2 + M);
-        const float4 c111 = Voxel<DT>::load(a.payload, v + M2 + M + 1);
+        const int vo = iz * M2 + iy * M + ix;  // voxel within the primitive
+        const int64_t v = (int64_t)k * M2 * M + vo;
+        const float4 c000 = Voxel<DT>::load(pbase, vo);
+        const float4 c001 = Voxel<DT>::load(pbase, vo + 1);
+        const float4 c010 = Voxel<DT>::load(pbase, vo + M);
+        const float4 c011 = Voxel<DT>::load(pbase, vo + M + 1);
+        const float4 c100 = Voxel<DT>::load(pbase, vo + M2);
+        const float4 c101 = Voxel<DT>::load(pbase, vo + M2 + 1);
+        const float4 c110 = Voxel<DT>::load(pbase, vo + M2 + M);
+        const float4 c111 = Voxel<DT>::load(pbase, vo + M2 + M + 1);
         const float4 c00 = lerp4(c000, c001, fx), c01 = lerp4(c010, c011, fx);
         const float4 c10 = lerp4(c100, c101, fx), c11 = lerp4(c110, c111, fx);
         const float4 c0 = lerp4(c00, c01, fy), c1 = lerp4(c10, c11, fy);
@@ -185,15 +187,14 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
 // g_j = sum dL/du_j:  dL/dt_m = -sum_j Mx_jm g_j;  dL/dR_mj = A_jm h / s_j;
 // dL/ds_j = -sum_m A_jm Mx_jm / s_j;  dL/dq through R(q/|q|).
 __global__ void k_pose_grads(const float *__restrict__ gmc, const Xform *__restrict__ xf,
-                             const Pose *__restrict__ pose, const float *__restrict__ q, int n, int M,
+                             const float *__restrict__ sv, const float *__restrict__ q, int n, int M,
                              float *__restrict__ g_t, float *__restrict__ g_q, float *__restrict__ g_s) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const float *A = gmc + 12 * (int64_t)k;
   const Xform X = xf[k];
   const float Mx[3][3] = {{X.r0.x, X.r0.y, X.r0.z}, {X.r1.x, X.r1.y, X.r1.z}, {X.r2.x, X.r2.y, X.r2.z}};
-  const Pose P = pose[k];
-  const float s[3] = {P.p3.x, P.p3.y, P.p3.z};
+  const float s[3] = {sv[3 * k], sv[3 * k + 1], sv[3 * k + 2]};
   const float h = 0.5f * (float)(M - 1);
   float G[9];  // dL/dR, row-major
 #pragma unroll
@@ -230,36 +231,46 @@ __global__ void k_pose_grads(const float *__restrict__ gmc, const Xform *__restr
   g_q[4 * k + 3] += (gz - z * dot) / nrm;
 }
 
-template <int DT, int CAP>
+template <int DT, int CAP, int MT>
 static cudaError_t launch_bwd_t(const BwdArgs &b, cudaStream_t st) {
   size_t smem = sizeof(TileShared<CAP>) * TILE_WARPS;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_backward<DT, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_backward<DT, CAP, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   int64_t blocks = (b.m.geom.n_warp_tiles + TILE_WARPS - 1) / TILE_WARPS;
-  if (blocks > 0) k_backward<DT, CAP><<<(unsigned)blocks, TILE_WARPS * 32, smem, st>>>(b);
+  if (blocks > 0) k_backward<DT, CAP, MT><<<(unsigned)blocks, TILE_WARPS * 32, smem, st>>>(b);
   return cudaGetLastError();
+}
+
+template <int DT>
+static cudaError_t launch_bwd_m(const BwdArgs &b, cudaStream_t st) {
+  switch (b.m.M) {
+    case 8: return launch_bwd_t<DT, MARCH_CAP, 8>(b, st);
+    case 16: return launch_bwd_t<DT, MARCH_CAP, 16>(b, st);
+    case 32: return launch_bwd_t<DT, MARCH_CAP, 32>(b, st);
+    default: return launch_bwd_t<DT, MARCH_CAP, 0>(b, st);
+  }
 }
 
 cudaError_t launch_backward(const BwdArgs &b, const float *t, const float *q, const float *s, float *g_t,
                             float *g_q, float *g_s, cudaStream_t st) {
   (void)t;
-  (void)s;
   if (b.gmc) cudaMemsetAsync(b.gmc, 0, sizeof(float) * 12 * (size_t)b.m.n_prims, st);
   cudaError_t e = cudaSuccess;
   switch (b.m.dtype) {
-    case MVP_F32: e = launch_bwd_t<MVP_F32, MARCH_CAP>(b, st); break;
-    case MVP_BF16: e = launch_bwd_t<MVP_BF16, MARCH_CAP>(b, st); break;
-    case MVP_F16: e = launch_bwd_t<MVP_F16, MARCH_CAP>(b, st); break;
+    case MVP_F32: e = launch_bwd_m<MVP_F32>(b, st); break;
+    case MVP_BF16: e = launch_bwd_m<MVP_BF16>(b, st); break;
+    case MVP_F16: e = launch_bwd_m<MVP_F16>(b, st); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
   if (b.gmc && b.m.n_prims > 0)
-    k_pose_grads<<<(b.m.n_prims + 255) / 256, 256, 0, st>>>(b.gmc, b.m.xf, b.m.pose, q, b.m.n_prims, b.m.M, g_t,
-                                                             g_q, g_s);
+    k_pose_grads<<<(b.m.n_prims + 255) / 256, 256, 0, st>>>(b.gmc, b.m.xf, s, q, b.m.n_prims, b.m.M, g_t, g_q,
+                                                             g_s);
   return cudaGetLastError();
 }
 

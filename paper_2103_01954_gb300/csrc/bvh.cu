@@ -82,7 +82,7 @@ __global__ void k_prims(const float *__restrict__ t, const float *__restrict__ q
   P.p0 = make_float4(R[0], R[1], R[2], R[3]);
   P.p1 = make_float4(R[4], R[5], R[6], R[7]);
   P.p2 = make_float4(R[8], tx, ty, tz);
-  P.p3 = make_float4(sx, sy, sz, 0.0f);
+  P.p3 = make_float4(__frcp_rn(sx), __frcp_rn(sy), __frcp_rn(sz), 0.0f);
   pose[k] = P;
   // u = diag(h/s) R^T (x - t) + h as rows {M_j0, M_j1, M_j2, c_j}, fixed rounding:
   // hs_j = h / s_j, M_jm = hs_j * R_mj, c_j = ((h - M_j0 t0) - M_j1 t1) - M_j2 t2.

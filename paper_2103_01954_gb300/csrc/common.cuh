@@ -1,9 +1,10 @@
 // common.cuh -- shared device definitions of the MVP ray-march library.
 //
-// Discrete decisions (Morton codes, ray/box membership) use explicit
-// round-to-nearest intrinsics (__fmul_rn, __fadd_rn, __fdiv_rn, __fsqrt_rn), which
-// the compiler never contracts into FMA, so their results are fixed bit for bit by
-// the operation order written here. Everything else may use FMA.
+// Discrete decisions (Morton codes, ray/box membership, the voxel cell of a sample)
+// use explicit round-to-nearest intrinsics (__fmul_rn, __fadd_rn, __fmaf_rn,
+// __frcp_rn, __fdiv_rn, __fsqrt_rn), which the compiler never contracts or
+// reassociates, so their results are fixed bit for bit by the operation order
+// written here. Everything else may use FMA.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -22,8 +23,8 @@ constexpr int STATUS_CAPACITY = 1;
 constexpr int STATUS_DEVICE = 2;
 
 // Per-primitive pose as used by the membership test: R (row-major, R[3*i+j]),
-// t, s. 64 bytes: p0 = {R00,R01,R02,R10}, p1 = {R11,R12,R20,R21},
-// p2 = {R22,t0,t1,t2}, p3 = {s0,s1,s2,0}.
+// t, 1/s (each correctly rounded). 64 bytes: p0 = {R00,R01,R02,R10},
+// p1 = {R11,R12,R20,R21}, p2 = {R22,t0,t1,t2}, p3 = {1/s0,1/s1,1/s2,0}.
 struct __align__(16) Pose {
   float4 p0, p1, p2, p3;
 };
@@ -75,29 +76,30 @@ __device__ __forceinline__ void rot_spec(float q0, float q1, float q2, float q3,
 }
 
 // Slab interval of ray (o, d) against the box of a pose in its local frame
-// ([-1,1]^3), clipped to [t_near, t_far]. Fixed operation order; returns hit.
+// ([-1,1]^3), clipped to [t_near, t_far]. Fixed operation order, every step
+// correctly rounded: p = o - t; per axis j the local origin and direction
+// ol = fma(R2j, p2, fma(R1j, p1, R0j*p0)) * (1/s_j), dl likewise with d; if dl == 0
+// the ray is inside the slab iff |ol| <= 1, else r = 1/dl, t1 = (-1 - ol)*r,
+// t2 = (1 - ol)*r. Returns whether [max(t_near, lows), min(t_far, highs)] is nonempty.
 __device__ __forceinline__ bool slab_spec(const Pose &P, float ox, float oy, float oz, float dx, float dy,
                                           float dz, float t_near, float t_far, float &tin, float &tout) {
   const float R[9] = {P.p0.x, P.p0.y, P.p0.z, P.p0.w, P.p1.x, P.p1.y, P.p1.z, P.p1.w, P.p2.x};
-  const float s[3] = {P.p3.x, P.p3.y, P.p3.z};
+  const float is[3] = {P.p3.x, P.p3.y, P.p3.z};
   float p0 = __fsub_rn(ox, P.p2.y), p1 = __fsub_rn(oy, P.p2.z), p2 = __fsub_rn(oz, P.p2.w);
   float lo = t_near, hi = t_far;
   bool ok = true;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
-    float on = __fmul_rn(R[0 * 3 + j], p0);
-    on = __fadd_rn(on, __fmul_rn(R[1 * 3 + j], p1));
-    on = __fadd_rn(on, __fmul_rn(R[2 * 3 + j], p2));
-    float dn = __fmul_rn(R[0 * 3 + j], dx);
-    dn = __fadd_rn(dn, __fmul_rn(R[1 * 3 + j], dy));
-    dn = __fadd_rn(dn, __fmul_rn(R[2 * 3 + j], dz));
-    float ol = __fdiv_rn(on, s[j]);
-    float dl = __fdiv_rn(dn, s[j]);
+    float on = __fmaf_rn(R[2 * 3 + j], p2, __fmaf_rn(R[1 * 3 + j], p1, __fmul_rn(R[0 * 3 + j], p0)));
+    float dn = __fmaf_rn(R[2 * 3 + j], dz, __fmaf_rn(R[1 * 3 + j], dy, __fmul_rn(R[0 * 3 + j], dx)));
+    float ol = __fmul_rn(on, is[j]);
+    float dl = __fmul_rn(dn, is[j]);
     if (dl == 0.0f) {
       if (ol < -1.0f || ol > 1.0f) ok = false;
     } else {
-      float t1 = __fdiv_rn(__fsub_rn(-1.0f, ol), dl);
-      float t2 = __fdiv_rn(__fsub_rn(1.0f, ol), dl);
+      float r = __frcp_rn(dl);
+      float t1 = __fmul_rn(__fsub_rn(-1.0f, ol), r);
+      float t2 = __fmul_rn(__fsub_rn(1.0f, ol), r);
       lo = fmaxf(lo, fminf(t1, t2));
       hi = fminf(hi, fmaxf(t1, t2));
     }

@@ -13,8 +13,41 @@
 
 namespace mvp {
 
-template <int DT, int CAP, bool COUNT>
-__global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_march(MarchArgs a) {
+// Voxel bytes per payload dtype.
+template <int DT>
+struct VoxelBytes {
+  static constexpr int value = DT == MVP_F32 ? 16 : 8;
+};
+
+// Gather the 8 voxels of the cell at (ix, iy, iz) of one primitive's payload and
+// interpolate RGBA. MT > 0 makes the payload edge a compile-time constant, so the
+// eight addresses are immediate offsets from one base.
+template <int DT, int MT>
+__device__ __forceinline__ float4 trilinear(const char *base, int Mr, int ix, int iy, int iz, float fx, float fy,
+                                            float fz) {
+  const int M = MT > 0 ? MT : Mr;
+  const int o = (iz * M + iy) * M + ix;
+  const void *p = base;
+  const float4 c000 = Voxel<DT>::load(p, o);
+  const float4 c001 = Voxel<DT>::load(p, o + 1);
+  const float4 c010 = Voxel<DT>::load(p, o + M);
+  const float4 c011 = Voxel<DT>::load(p, o + M + 1);
+  const float4 c100 = Voxel<DT>::load(p, o + M * M);
+  const float4 c101 = Voxel<DT>::load(p, o + M * M + 1);
+  const float4 c110 = Voxel<DT>::load(p, o + M * M + M);
+  const float4 c111 = Voxel<DT>::load(p, o + M * M + M + 1);
+  const float4 c00 = lerp4(c000, c001, fx), c01 = lerp4(c010, c011, fx);
+  const float4 c10 = lerp4(c100, c101, fx), c11 = lerp4(c110, c111, fx);
+  const float4 c0 = lerp4(c00, c01, fy), c1 = lerp4(c10, c11, fy);
+  return lerp4(c0, c1, fz);
+}
+
+#ifndef MVP_MARCH_MINB
+#define MVP_MARCH_MINB 5
+#endif
+
+template <int DT, int CAP, bool COUNT, int MT>
+__global__ void __launch_bounds__(TILE_WARPS * 32, MVP_MARCH_MINB) k_march(MarchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   TileShared<CAP> &sh = reinterpret_cast<TileShared<CAP> *>(smem_raw)[warp];
@@ -26,23 +59,21 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_march(MarchArgs a) {
   if (__ballot_sync(FULL, valid) == 0) return;
 
   float T = 0.0f, Ir = 0.0f, Ig = 0.0f, Ib = 0.0f;
-  int i_last = a.n_steps - 1, i_clamp = -1;
-  float rho_r = 0.0f, rho_g = 0.0f, rho_b = 0.0f, beta = 0.0f;
   int n_eval = 0;
   bool alive = valid && a.n_steps > 0 && a.n_prims > 0;
+  bool saved_done = false;
 
-  Packet P;
-  make_packet(P, valid, L.o, L.d, a.t_far);
-  const int M = a.M, M2 = M * M;
+  make_packet(sh.pk, valid, L.o, L.d, a.t_far);
+  const int M = MT > 0 ? MT : a.M;
   const float Mm1 = (float)(M - 1);
-  const int64_t M3 = (int64_t)M2 * M;
+  const int64_t prim_bytes = (int64_t)M * M * M * VoxelBytes<DT>::value;
 
   int w0 = 0, wlen = a.n_steps;
   while (w0 < a.n_steps && __any_sync(FULL, alive)) {
     int w1 = min(a.n_steps, w0 + wlen);
     int lane_last = alive ? a.n_steps - 1 : -1;
-    int ne = build_window<CAP>(sh, a.nodes, a.pose, a.xf, a.n_prims, P, L, lane_last, a.t_near, a.t_far, a.dt,
-                               a.n_steps, w0, w1);
+    int ne = build_window<CAP>(sh, a.nodes, a.pose, a.xf, reinterpret_cast<const char *>(a.payload), prim_bytes,
+                               a.n_prims, L, lane_last, a.t_near, a.t_far, a.dt, a.n_steps, w0, w1);
     if (ne < 0) {
       if (w1 - w0 == 1) {  // one sample overlapped by more than CAP primitives
         if (lane == 0) atomicOr(a.status, STATUS_CAPACITY);
@@ -77,7 +108,8 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_march(MarchArgs a) {
           const bool in = alive && i >= (int)(rg & 0xffffu) && i <= (int)(rg >> 16);
           if (in) {
             const Xform X = sh.exf[e];
-            const int k = sh.ek[e];
+            // voxel coordinate u = Mx x + c (FP32, the cell decision of the oracle's
+            // FP32 mode), clamped into the box
             float ux = fmaf(X.r0.x, x0, fmaf(X.r0.y, x1, fmaf(X.r0.z, x2, X.r0.w)));
             float uy = fmaf(X.r1.x, x0, fmaf(X.r1.y, x1, fmaf(X.r1.z, x2, X.r1.w)));
             float uz = fmaf(X.r2.x, x0, fmaf(X.r2.y, x1, fmaf(X.r2.z, x2, X.r2.w)));
@@ -85,20 +117,8 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_march(MarchArgs a) {
             uy = fminf(fmaxf(uy, 0.0f), Mm1);
             uz = fminf(fmaxf(uz, 0.0f), Mm1);
             const int ix = min((int)ux, M - 2), iy = min((int)uy, M - 2), iz = min((int)uz, M - 2);
-            const float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
-            const int64_t v = (int64_t)k * M3 + (int64_t)(iz * M2 + iy * M + ix);
-            const float4 c000 = Voxel<DT>::load(a.payload, v);
-            const float4 c001 = Voxel<DT>::load(a.payload, v + 1);
-            const float4 c010 = Voxel<DT>::load(a.payload, v + M);
-            const float4 c011 = Voxel<DT>::load(a.payload, v + M + 1);
-            const float4 c100 = Voxel<DT>::load(a.payload, v + M2);
-            const float4 c101 = Voxel<DT>::load(a.payload, v + M2 + 1);
-            const float4 c110 = Voxel<DT>::load(a.payload, v + M2 + M);
-            const float4 c111 = Voxel<DT>::load(a.payload, v + M2 + M + 1);
-            const float4 c00 = lerp4(c000, c001, fx), c01 = lerp4(c010, c011, fx);
-            const float4 c10 = lerp4(c100, c101, fx), c11 = lerp4(c110, c111, fx);
-            const float4 c0 = lerp4(c00, c01, fy), c1 = lerp4(c10, c11, fy);
-            const float4 val = lerp4(c0, c1, fz);
+            const float4 val = trilinear<DT, MT>(sh.eptr[e], M, ix, iy, iz, ux - (float)ix, uy - (float)iy,
+                                                 uz - (float)iz);
             sa += val.w;
             sr = fmaf(val.w, val.x, sr);
             sg = fmaf(val.w, val.y, sg);
@@ -107,6 +127,7 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_march(MarchArgs a) {
           }
         }
         if (alive) {
+          // clamped additive accumulation: w = min(a, 1 - T), I += c w / a, T += w
           const float aa = sa * a.dt;
           const float cr = sr * a.dt, cg = sg * a.dt, cb = sb * a.dt;
           const float rem = 1.0f - T;
@@ -115,21 +136,26 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_march(MarchArgs a) {
             Ig += cg;
             Ib += cb;
             T = fminf(T + aa, 1.0f);
+            if (T >= a.stop_T) {
+              alive = false;
+              if (!COUNT && a.saved) {
+                Saved S = {0.0f, 0.0f, 0.0f, 0.0f, i, -1};
+                a.saved[L.r] = S;
+              }
+              saved_done = true;
+            }
           } else {
             const float bt = rem / aa;
             Ir = fmaf(cr, bt, Ir);
             Ig = fmaf(cg, bt, Ig);
             Ib = fmaf(cb, bt, Ib);
-            i_clamp = i;
-            rho_r = cr / aa;
-            rho_g = cg / aa;
-            rho_b = cb / aa;
-            beta = bt;
             T = 1.0f;
-          }
-          if (T >= a.stop_T) {
-            alive = false;
-            i_last = i;
+            alive = false;  // T = 1 >= 1 - eps_early
+            if (!COUNT && a.saved) {
+              Saved S = {cr / aa, cg / aa, cb / aa, bt, i, i};
+              a.saved[L.r] = S;
+            }
+            saved_done = true;
           }
         }
       }
@@ -145,14 +171,8 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_march(MarchArgs a) {
   const float bgw = 1.0f - T;
   float4 out = make_float4(fmaf(bgw, a.bg[0], Ir), fmaf(bgw, a.bg[1], Ig), fmaf(bgw, a.bg[2], Ib), T);
   reinterpret_cast<float4 *>(a.out)[L.r] = out;
-  if (a.saved) {
-    Saved S;
-    S.rho_r = rho_r;
-    S.rho_g = rho_g;
-    S.rho_b = rho_b;
-    S.beta = beta;
-    S.i_last = i_last;
-    S.i_clamp = i_clamp;
+  if (a.saved && !saved_done) {
+    Saved S = {0.0f, 0.0f, 0.0f, 0.0f, a.n_steps - 1, -1};
     a.saved[L.r] = S;
   }
 }
@@ -172,8 +192,7 @@ __global__ void __launch_bounds__(TILE_WARPS * 32) k_hits(HitArgs a) {
   load_lane_ray(L, a.o, a.d, tile_ray(a.geom, wt, lane));
   const bool valid = L.r >= 0;
   if (__ballot_sync(FULL, valid) == 0) return;
-  Packet P;
-  make_packet(P, valid, L.o, L.d, a.t_far);
+  make_packet(sh.pk, valid, L.o, L.d, a.t_far);
   int64_t count = 0;
   const int64_t base = (FILL && valid) ? a.offs[L.r] : 0;
   float ta = a.t_near, span = a.t_far - a.t_near;
@@ -210,7 +229,7 @@ __global__ void __launch_bounds__(TILE_WARPS * 32) k_hits(HitArgs a) {
       return true;
     };
     float slack = 1.0e-5f * (fabsf(ta) + fabsf(tb)) + 1.0e-30f;
-    bool ok = traverse_tile(sh, a.nodes, a.n_prims, P, ta - slack, tb + slack, emit);
+    bool ok = traverse_tile(sh, a.nodes, a.n_prims, ta - slack, tb + slack, emit);
     __syncwarp();
     if (!ok) {
       count = c0;  // drop this window's partial output and retry a narrower one
@@ -267,28 +286,38 @@ __global__ void __launch_bounds__(1024) k_offsets(const int64_t *__restrict__ co
 }
 
 // ----------------------------------------------------------------------------
-template <int DT, int CAP, bool COUNT>
+template <int DT, int CAP, bool COUNT, int MT>
 static cudaError_t launch_march_t(const MarchArgs &a, cudaStream_t st) {
   size_t smem = sizeof(TileShared<CAP>) * TILE_WARPS;
   static bool attr_set = false;  // per instantiation; set once per process
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_march<DT, CAP, COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_march<DT, CAP, COUNT, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   int64_t blocks = (a.geom.n_warp_tiles + TILE_WARPS - 1) / TILE_WARPS;
   if (blocks == 0) return cudaSuccess;
-  k_march<DT, CAP, COUNT><<<(unsigned)blocks, TILE_WARPS * 32, smem, st>>>(a);
+  k_march<DT, CAP, COUNT, MT><<<(unsigned)blocks, TILE_WARPS * 32, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+template <int DT, bool COUNT>
+static cudaError_t launch_march_m(const MarchArgs &a, cudaStream_t st) {
+  switch (a.M) {
+    case 8: return launch_march_t<DT, MARCH_CAP, COUNT, 8>(a, st);
+    case 16: return launch_march_t<DT, MARCH_CAP, COUNT, 16>(a, st);
+    case 32: return launch_march_t<DT, MARCH_CAP, COUNT, 32>(a, st);
+    default: return launch_march_t<DT, MARCH_CAP, COUNT, 0>(a, st);
+  }
 }
 
 template <bool COUNT>
 static cudaError_t launch_march_c(const MarchArgs &a, cudaStream_t st) {
   switch (a.dtype) {
-    case MVP_F32: return launch_march_t<MVP_F32, MARCH_CAP, COUNT>(a, st);
-    case MVP_BF16: return launch_march_t<MVP_BF16, MARCH_CAP, COUNT>(a, st);
-    case MVP_F16: return launch_march_t<MVP_F16, MARCH_CAP, COUNT>(a, st);
+    case MVP_F32: return launch_march_m<MVP_F32, COUNT>(a, st);
+    case MVP_BF16: return launch_march_m<MVP_BF16, COUNT>(a, st);
+    case MVP_F16: return launch_march_m<MVP_F16, COUNT>(a, st);
   }
   return cudaErrorInvalidValue;
 }

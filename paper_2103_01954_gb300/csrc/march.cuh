@@ -5,7 +5,10 @@
 
 namespace mvp {
 
-constexpr int MARCH_CAP = 64;  // primitives a warp tile holds per depth window
+#ifndef MVP_MARCH_CAP
+#define MVP_MARCH_CAP 48
+#endif
+constexpr int MARCH_CAP = MVP_MARCH_CAP;  // primitives a warp tile holds per depth window
 
 struct MarchArgs {
   // primitives and their BVH

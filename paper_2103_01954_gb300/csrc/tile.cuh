@@ -65,6 +65,7 @@ struct Packet {
 };
 
 __device__ __forceinline__ void make_packet(Packet &P, bool valid, const float o[3], const float d[3], float t_far) {
+  // every lane computes the same values; the caller's P may be warp-shared memory
   float om = 0.0f, dm = 0.0f;
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
@@ -88,6 +89,7 @@ __device__ __forceinline__ void make_packet(Packet &P, bool valid, const float o
     }
   }
   P.margin = 1.0e-5f * (om + fabsf(t_far) * dm) + 1.0e-30f;
+  __syncwarp();
 }
 
 // Can some ray of the packet meet the (inflated) box for t in [ta, tb]?
@@ -116,17 +118,29 @@ __device__ __forceinline__ bool packet_hits_box(const Packet &P, float4 a, float
       tmin = fmaxf(tmin, te);
       tmax = fminf(tmax, tx);
     }
-    // sgn == 0: a ray parallel to the slab may lie inside it for every t
+    else {
+      // directions straddle zero on this axis, so no t-bound follows from it; bound
+      // the coordinate o_j + t d_j itself over the window (extremes at the corners
+      // of [omin, omax] x [ta, tb] x [dmin, dmax])
+      float c0 = fminf(fminf(fmaf(ta, P.dmin[j], P.omin[j]), fmaf(tb, P.dmin[j], P.omin[j])),
+                       fminf(fmaf(ta, P.dmax[j], P.omin[j]), fmaf(tb, P.dmax[j], P.omin[j])));
+      float c1 = fmaxf(fmaxf(fmaf(ta, P.dmin[j], P.omax[j]), fmaf(tb, P.dmin[j], P.omax[j])),
+                       fmaxf(fmaf(ta, P.dmax[j], P.omax[j]), fmaf(tb, P.dmax[j], P.omax[j])));
+      if (c1 < l || c0 > h) return false;
+    }
   }
   return tmin <= tmax + 1.0e-5f * (fabsf(tmax) + fabsf(tmin)) + 1.0e-30f;
 }
 
-// Warp-private shared memory of a tile.
+// Warp-private shared memory of a tile. The packet bounds are warp-uniform, so
+// they live here rather than in every lane's registers.
 template <int CAP>
 struct TileShared {
+  Packet pk;
   int stack[STACK];
   int cand[CBUF];
   Xform exf[CAP];
+  const char *eptr[CAP];  // payload of the entry's primitive
   int ek[CAP];
   int elo[CAP], ehi[CAP];
   uint32_t erng[CAP][32];
@@ -136,8 +150,9 @@ struct TileShared {
 // are passed to `emit(nc)` in batches of up to CBUF via sh.cand; emit returns false
 // to abort. Returns false on stack overflow or an aborted emit.
 template <class SH, class Emit>
-__device__ __forceinline__ bool traverse_tile(SH &sh, const Node *__restrict__ nodes, int n_prims,
-                                              const Packet &P, float ta, float tb, Emit &&emit) {
+__device__ __forceinline__ bool traverse_tile(SH &sh, const Node *__restrict__ nodes, int n_prims, float ta,
+                                              float tb, Emit &&emit) {
+  const Packet &P = sh.pk;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   if (n_prims <= 0) return true;
@@ -211,8 +226,9 @@ __device__ __forceinline__ void load_lane_ray(LaneRay &L, const float *__restric
 template <int CAP>
 __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__restrict__ nodes,
                                             const Pose *__restrict__ pose, const Xform *__restrict__ xf,
-                                            int n_prims, const Packet &P, const LaneRay &L, int lane_last,
-                                            float t_near, float t_far, float dt, int n_steps, int w0, int w1) {
+                                            const char *payload, int64_t prim_bytes, int n_prims,
+                                            const LaneRay &L, int lane_last, float t_near, float t_far, float dt,
+                                            int n_steps, int w0, int w1) {
   const int lane = threadIdx.x & 31;
   float ta = sample_t(t_near, dt, w0);
   float tb = sample_t(t_near, dt, w1 - 1);
@@ -250,6 +266,7 @@ __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__r
         sh.exf[ne].r0 = __ldg(xp);
         sh.exf[ne].r1 = __ldg(xp + 1);
         sh.exf[ne].r2 = __ldg(xp + 2);
+        sh.eptr[ne] = payload + (int64_t)k * prim_bytes;
       }
       ++ne;
     }
@@ -257,7 +274,7 @@ __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__r
   };
   // the packet test uses the window's time range with a small slack
   float slack = 1.0e-5f * (fabsf(ta) + fabsf(tb)) + 1.0e-30f;
-  bool ok = traverse_tile(sh, nodes, n_prims, P, ta - slack, tb + slack, emit);
+  bool ok = traverse_tile(sh, nodes, n_prims, ta - slack, tb + slack, emit);
   __syncwarp();
   return ok ? ne : -1;
 }

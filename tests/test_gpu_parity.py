@@ -252,8 +252,11 @@ def test_capacity_overflow_reports_error():
         dv.ctx.sync()
     assert ei.value.status == B.MVP_ERR_CAPACITY
     dv.ctx.sync()  # the status word was cleared; the context stays usable
-    # 60 overlapping primitives fit
-    sc60 = synthetic.Scene(t=sc.t[:60], q=sc.q[:60], s=sc.s[:60], payload=sc.payload[:60], M=3)
+    # as many overlapping primitives as a tile holds still render correctly
+    from paper_2103_01954_gb300 import build as bld
+    import re
+    cap = int(re.search(r"define MVP_MARCH_CAP (\d+)", open(bld.CSRC + "/march.cuh").read()).group(1))
+    sc60 = synthetic.Scene(t=sc.t[:cap], q=sc.q[:cap], s=sc.s[:cap], payload=sc.payload[:cap], M=3)
     out, _ = Dev(sc60, rays).build().render()
     ref = oracle.render(sc60, rays, F32M)["rgba"]
     assert np.abs(out.cpu().numpy() - ref).max() < 1e-4
