@@ -195,6 +195,28 @@ MVP_API mvp_status mvp_pack_payload(mvp_ctx *ctx, const float *src, void *dst, i
 MVP_API mvp_status mvp_camera_rays(mvp_ctx *ctx, const float *c2w, float focal, int32_t width, int32_t height,
                            float *o, float *d, mvp_stream stream);
 
+/* ------------------------------------------------ allocation-free render */
+/* No counterpart in the paper. For callers that cannot allocate device memory:
+ * a plug-in inside a host application that owns every device allocation, a
+ * real-time frame loop that must not stall on the implicit synchronisation of
+ * cudaMalloc/cudaFree, or a component whose memory budget is fixed at start-up.
+ * Rebuilds the BVH of `prims` and renders `rays` into out_rgba (device, [n][4])
+ * exactly as mvp_build_bvh + mvp_raymarch_fwd would, on the current CUDA device,
+ * without a context or handle and without allocating: the BVH and the status word
+ * live in a file-scope device array sized for MVP_STATIC_MAX_PRIMS primitives
+ * (about 4 MB, held by every GPU that loads the library until the process exits).
+ * Returns MVP_ERR_INVALID_ARG for more primitives than that (or any other bad
+ * argument), before launching anything. The first call on a device looks up the
+ * array's device address, so make it before any stream capture. Every call reuses
+ * the same array and it keeps the last call's contents; calls whose GPU work
+ * overlaps (other streams or threads) race on it and must be serialised by the
+ * caller. status_out (device int32, nullable) receives the kernels' status bits
+ * (1: more primitives overlapped one sample of a ray tile than a tile holds).
+ * Asynchronous on `stream`; no adjoint state is saved. */
+#define MVP_STATIC_MAX_PRIMS 16384
+MVP_API mvp_status mvp_raymarch_fwd_static(const mvp_prims *prims, const mvp_rays *rays, float *out_rgba,
+                                           int32_t *status_out, mvp_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

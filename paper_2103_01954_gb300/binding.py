@@ -71,6 +71,8 @@ _SIGS = [
     ("mvp_pack_payload", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p]),
     ("mvp_camera_rays", c_int32, [c_void_p, ctypes.POINTER(c_float), c_float, c_int32, c_int32, c_void_p,
                                   c_void_p, c_void_p]),
+    ("mvp_raymarch_fwd_static", c_int32, [ctypes.POINTER(mvp_prims), ctypes.POINTER(mvp_rays), c_void_p, c_void_p,
+                                          c_void_p]),
 ]
 
 

@@ -129,6 +129,11 @@ struct DeviceGuard {
 
 }  // namespace
 
+namespace mvp {
+// Lets other translation units of the library set the message mvp_last_error() returns.
+void record_error(const char *msg) { g_err = msg; }
+}  // namespace mvp
+
 extern "C" {
 
 const char *mvp_version(void) { return "mvp-gb300 1.0 (abi 1, sm_103a)"; }

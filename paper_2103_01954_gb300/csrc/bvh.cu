@@ -131,6 +131,7 @@ __global__ void k_prims(const float *__restrict__ t, const float *__restrict__ q
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_ITEMS = 8;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+static_assert(SORT_TILE == BVH_SORT_TILE, "BVH_SORT_TILE sizes the digit-count buffers");
 
 __global__ void __launch_bounds__(SORT_THREADS) k_sort_count(const uint32_t *__restrict__ keys, int n, int shift,
                                                              int nblocks, int *__restrict__ counts) {

@@ -5,6 +5,8 @@
 
 namespace mvp {
 
+constexpr int BVH_SORT_TILE = 2048;  // keys per radix-sort block (sizes BvhBuffers::counts)
+
 struct BvhBuffers {
   char *base = nullptr;
   size_t bytes = 0;
