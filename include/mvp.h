@@ -195,6 +195,65 @@ MVP_API mvp_status mvp_pack_payload(mvp_ctx *ctx, const float *src, void *dst, i
 MVP_API mvp_status mvp_camera_rays(mvp_ctx *ctx, const float *c2w, float focal, int32_t width, int32_t height,
                            float *o, float *d, mvp_stream stream);
 
+/* ------------------------------------------------------------ serving */
+/* Continuous batching of render requests (avatar = resident primitive set,
+ * camera, resolution) through one persistent kernel. Each admitted request is cut
+ * into 8x4-pixel warp tiles numbered in one global sequence; worker warps claim
+ * tile numbers, generate the tile's pinhole rays and march it with the code of
+ * mvp_raymarch_fwd, so a request's image equals mvp_camera_rays + mvp_raymarch_fwd
+ * on the same avatar. Requests published while a worker grid runs are picked up by
+ * its warps as they free up (requests overlap on the device); no device code waits
+ * for anything. Admission: a request needs a free slot, and its image
+ * (width*height*16 bytes) must fit the HBM budget (resident avatars + images in
+ * flight) and the server's image arena; otherwise it queues (FIFO) and is admitted
+ * by a later submit or poll. All calls are thread-safe. */
+typedef struct mvp_server mvp_server;
+
+typedef struct mvp_request {
+  int32_t avatar;        /* id from mvp_serve_register_avatar */
+  int32_t width, height; /* image size in pixels (>= 1) */
+  float focal;           /* pixels */
+  float c2w[12];         /* row-major 3x4 [right down forward | eye], as mvp_camera_rays */
+  float t_near, t_far, dt, eps_early;
+  float bg[3];
+} mvp_request;
+
+typedef struct mvp_serve_info {
+  int64_t pending, in_flight, max_in_flight, completed;
+  int64_t resident_bytes, in_flight_bytes;
+  int32_t grid_blocks, avatars;
+  int32_t device_status;  /* status bits set by the serving kernel (0: none) */
+  int32_t reserved;
+} mvp_serve_info;
+
+/* hbm_budget: bytes for resident avatars (payload + BVH) plus images in flight;
+ * max_slots: requests in flight at once (1..65536); arena_bytes: device memory
+ * allocated up front for images in flight (0: the budget; capped by it). */
+MVP_API mvp_status mvp_serve_create(mvp_ctx *ctx, size_t hbm_budget, int32_t max_slots, size_t arena_bytes,
+                                    mvp_server **out);
+/* Waits for the server's device work, then frees it (avatars' payloads stay the
+ * caller's). */
+MVP_API void mvp_serve_destroy(mvp_server *server);
+/* Keeps `prims` (device pointers, caller-owned, must stay valid) resident and builds
+ * its BVH once (avatars do not move between requests). Synchronises.
+ * MVP_ERR_CAPACITY if it does not fit the budget. */
+MVP_API mvp_status mvp_serve_register_avatar(mvp_server *server, const mvp_prims *prims, int32_t *avatar_id);
+/* Queues a request and admits what fits; *ticket identifies it. MVP_ERR_CAPACITY
+ * if the image alone exceeds the budget or the arena; MVP_ERR_INVALID_ARG for a
+ * bad avatar or parameters. */
+MVP_API mvp_status mvp_serve_submit(mvp_server *server, const mvp_request *req, uint64_t *ticket);
+/* Non-blocking: MVP_NOT_READY while the request is queued or running; MVP_OK once
+ * done, after copying the image ([h][w][4] float32) to out_rgba (device or host
+ * pointer, or NULL to drop it) and releasing its slot and memory. latency_ms
+ * (nullable) = host time from submit until this poll saw it done. */
+MVP_API mvp_status mvp_serve_poll(mvp_server *server, uint64_t ticket, float *out_rgba, double *latency_ms);
+/* Polls until done or timeout_ms passes (MVP_ERR_TIMEOUT, request still queued or
+ * running). */
+MVP_API mvp_status mvp_serve_wait(mvp_server *server, uint64_t ticket, double timeout_ms, float *out_rgba,
+                                  double *latency_ms);
+/* Counters, and the kernel status bits (reads the device status word). */
+MVP_API mvp_status mvp_serve_stats(mvp_server *server, mvp_serve_info *info);
+
 /* ------------------------------------------------ allocation-free render */
 /* No counterpart in the paper. For callers that cannot allocate device memory:
  * a plug-in inside a host application that owns every device allocation, a

@@ -37,6 +37,18 @@ class mvp_rays(ctypes.Structure):
                 ("height", c_int32)]
 
 
+class mvp_request(ctypes.Structure):
+    _fields_ = [("avatar", c_int32), ("width", c_int32), ("height", c_int32), ("focal", c_float),
+                ("c2w", c_float * 12), ("t_near", c_float), ("t_far", c_float), ("dt", c_float),
+                ("eps_early", c_float), ("bg", c_float * 3)]
+
+
+class mvp_serve_info(ctypes.Structure):
+    _fields_ = [("pending", c_int64), ("in_flight", c_int64), ("max_in_flight", c_int64), ("completed", c_int64),
+                ("resident_bytes", c_int64), ("in_flight_bytes", c_int64), ("grid_blocks", c_int32),
+                ("avatars", c_int32), ("device_status", c_int32), ("reserved", c_int32)]
+
+
 class MVPError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{message} [{status}]")
@@ -71,6 +83,14 @@ _SIGS = [
     ("mvp_pack_payload", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_void_p]),
     ("mvp_camera_rays", c_int32, [c_void_p, ctypes.POINTER(c_float), c_float, c_int32, c_int32, c_void_p,
                                   c_void_p, c_void_p]),
+    ("mvp_serve_create", c_int32, [c_void_p, c_size_t, c_int32, c_size_t, ctypes.POINTER(c_void_p)]),
+    ("mvp_serve_destroy", None, [c_void_p]),
+    ("mvp_serve_register_avatar", c_int32, [c_void_p, ctypes.POINTER(mvp_prims), ctypes.POINTER(c_int32)]),
+    ("mvp_serve_submit", c_int32, [c_void_p, ctypes.POINTER(mvp_request), ctypes.POINTER(ctypes.c_uint64)]),
+    ("mvp_serve_poll", c_int32, [c_void_p, ctypes.c_uint64, c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    ("mvp_serve_wait", c_int32, [c_void_p, ctypes.c_uint64, ctypes.c_double, c_void_p,
+                                 ctypes.POINTER(ctypes.c_double)]),
+    ("mvp_serve_stats", c_int32, [c_void_p, ctypes.POINTER(mvp_serve_info)]),
     ("mvp_raymarch_fwd_static", c_int32, [ctypes.POINTER(mvp_prims), ctypes.POINTER(mvp_rays), c_void_p, c_void_p,
                                           c_void_p]),
 ]

@@ -132,6 +132,7 @@ struct DeviceGuard {
 namespace mvp {
 // Lets other translation units of the library set the message mvp_last_error() returns.
 void record_error(const char *msg) { g_err = msg; }
+int ctx_device(const mvp_ctx *ctx) { return ctx->device; }
 }  // namespace mvp
 
 extern "C" {

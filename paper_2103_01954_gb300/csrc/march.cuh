@@ -56,6 +56,7 @@ struct BwdArgs {
 
 cudaError_t launch_march(const MarchArgs &a, cudaStream_t st);
 void record_error(const char *msg);
+int ctx_device(const mvp_ctx *ctx);
 cudaError_t launch_hits(const HitArgs &a, int64_t *counts, cudaStream_t st);
 cudaError_t launch_hits_fill(const HitArgs &a, cudaStream_t st);
 cudaError_t launch_backward(const BwdArgs &a, const float *t, const float *q, const float *s, float *g_t,

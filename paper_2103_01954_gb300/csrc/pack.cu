@@ -1,5 +1,6 @@
 // pack.cu -- payload precision conversion and pinhole camera rays.
 #include "pack.cuh"
+#include "camera.cuh"
 
 namespace mvp {
 
@@ -41,24 +42,19 @@ cudaError_t launch_pack(const float *src, void *dst, int64_t n, int dtype, cudaS
   return cudaGetLastError();
 }
 
-// Pinhole rays: d = normalize(right * (col + 0.5 - W/2)/f + down * (row + 0.5 - H/2)/f + forward).
+// Pinhole rays of a W x H image, row-major (camera_ray in camera.cuh).
 __global__ void k_camera(Cam c, float *__restrict__ o, float *__restrict__ d) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t n = (int64_t)c.width * c.height;
   if (i >= n) return;
   int row = (int)(i / c.width), col = (int)(i - (int64_t)row * c.width);
-  float cx = ((float)col + 0.5f - 0.5f * (float)c.width) / c.focal;
-  float cy = ((float)row + 0.5f - 0.5f * (float)c.height) / c.focal;
-  float dx = c.m[0] * cx + c.m[1] * cy + c.m[2];
-  float dy = c.m[4] * cx + c.m[5] * cy + c.m[6];
-  float dz = c.m[8] * cx + c.m[9] * cy + c.m[10];
-  float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-  o[3 * i] = c.m[3];
-  o[3 * i + 1] = c.m[7];
-  o[3 * i + 2] = c.m[11];
-  d[3 * i] = dx * inv;
-  d[3 * i + 1] = dy * inv;
-  d[3 * i + 2] = dz * inv;
+  float oo[3], dd[3];
+  camera_ray(c.m, c.focal, c.width, c.height, row, col, oo, dd);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    o[3 * i + j] = oo[j];
+    d[3 * i + j] = dd[j];
+  }
 }
 
 cudaError_t launch_camera(const Cam &c, float *o, float *d, cudaStream_t st) {

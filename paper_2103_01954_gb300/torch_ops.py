@@ -224,3 +224,68 @@ class MVPRender(torch.autograd.Function):
 
 def render(t, q, s, payload, o, d, params: dict, ctx: Context, bvh: BVH):
     return MVPRender.apply(t, q, s, payload, o, d, params, ctx, bvh)
+
+
+class Server:
+    """mvp_server: continuous batching of render requests over resident avatars."""
+
+    def __init__(self, ctx: Context, hbm_budget: int, max_slots: int = 64, arena_bytes: int = 0):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        B.check(B.lib().mvp_serve_create(ctx.handle, int(hbm_budget), int(max_slots), int(arena_bytes),
+                                         ctypes.byref(h)), "mvp_serve_create")
+        self.handle = h
+        self._keep = []  # avatar tensors must outlive the server
+
+    def register(self, t, q, s, payload) -> int:
+        prims = prims_struct(t, q, s, payload)
+        aid = ctypes.c_int32(-1)
+        B.check(B.lib().mvp_serve_register_avatar(self.handle, ctypes.byref(prims), ctypes.byref(aid)),
+                "mvp_serve_register_avatar")
+        self._keep.append((t, q, s, payload))
+        return aid.value
+
+    @staticmethod
+    def request(avatar: int, c2w, focal: float, width: int, height: int, t_near: float, t_far: float, dt: float,
+                eps_early: float = 0.0, bg=(0.0, 0.0, 0.0)) -> B.mvp_request:
+        r = B.mvp_request(avatar=avatar, width=width, height=height, focal=focal, t_near=t_near, t_far=t_far, dt=dt,
+                          eps_early=eps_early)
+        for i, v in enumerate([float(x) for x in list(c2w.reshape(-1))]):
+            r.c2w[i] = v
+        r.bg[0], r.bg[1], r.bg[2] = bg
+        return r
+
+    def submit_raw(self, req: B.mvp_request) -> int:
+        """Returns the ticket; raises on refusal."""
+        tk = ctypes.c_uint64(0)
+        B.check(B.lib().mvp_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(tk)), "mvp_serve_submit")
+        return tk.value
+
+    def poll(self, ticket: int, out=None):
+        """(status, latency_ms); status is MVP_OK or MVP_NOT_READY."""
+        lat = ctypes.c_double(0.0)
+        st = B.lib().mvp_serve_poll(self.handle, ticket, _ptr(out), ctypes.byref(lat))
+        if st < 0:
+            B.check(st, "mvp_serve_poll")
+        return st, lat.value
+
+    def wait(self, ticket: int, timeout_ms: float, out=None):
+        lat = ctypes.c_double(0.0)
+        st = B.lib().mvp_serve_wait(self.handle, ticket, float(timeout_ms), _ptr(out), ctypes.byref(lat))
+        return st, lat.value
+
+    def stats(self) -> dict:
+        info = B.mvp_serve_info()
+        B.check(B.lib().mvp_serve_stats(self.handle, ctypes.byref(info)), "mvp_serve_stats")
+        return {k: getattr(info, k) for k, _ in B.mvp_serve_info._fields_}
+
+    def close(self):
+        if self.handle:
+            B.lib().mvp_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,151 @@
+"""Serving (continuous batching through one persistent kernel).
+
+Each request's image must equal mvp_camera_rays + mvp_raymarch_fwd on the same
+avatar, and must be the same whether the request runs alone or in a mix of many
+concurrent requests of other avatars, cameras and resolutions. Admission honours
+the HBM budget; oversize requests are refused; waits time out on the host.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from gpu_util import DEV  # noqa: E402
+from paper_2103_01954_gb300 import binding as B  # noqa: E402
+from paper_2103_01954_gb300 import torch_ops as T  # noqa: E402
+
+T_NEAR, T_FAR, DT = 1.0, 5.0, 0.01
+
+
+def _avatars(ctx):
+    """Three small avatars of different sizes and payload types (FP32, BF16, FP16)."""
+    specs = [(256, 8, torch.float32, 0), (1024, 6, torch.bfloat16, 1), (64, 16, torch.float16, 2)]
+    out = []
+    for n, M, dt, seed in specs:
+        sc = synthetic.make_scene(n, M, seed, layout="shell", s_range=(0.04 * (4096 / n) ** 0.5, 0.08 * (4096 / n) ** 0.5))
+        t = torch.from_numpy(sc.t).to(DEV)
+        q = torch.from_numpy(sc.q).to(DEV)
+        s = torch.from_numpy(sc.s).to(DEV)
+        p32 = torch.from_numpy(sc.payload).to(DEV)
+        p = p32 if dt == torch.float32 else T.pack_payload(ctx, p32, dt)
+        out.append((t, q, s, p))
+    return out
+
+
+def _reference(ctx, av, cam, focal, w, h):
+    t, q, s, p = av
+    prims = T.prims_struct(t, q, s, p)
+    bvh = T.BVH(ctx)
+    bvh.build(prims)
+    o, d = T.camera_rays(ctx, cam, focal, w, h)
+    rs = T.rays_struct(o, d, t_near=T_NEAR, t_far=T_FAR, dt=DT, width=w, height=h)
+    out, _ = T.raymarch_fwd(ctx, prims, bvh, rs)
+    ctx.sync()
+    return out
+
+
+def _cams(n, seed):
+    rng = np.random.default_rng(seed)
+    return [synthetic.random_camera(rng, 3.0, 1, 1, 1.0).matrix34() for _ in range(n)]
+
+
+def test_serving_matches_single_render_and_mix():
+    torch.cuda.set_device(0)
+    ctx = T.Context(0)
+    avs = _avatars(ctx)
+    srv = T.Server(ctx, hbm_budget=2 << 30, max_slots=16)
+    ids = [srv.register(*a) for a in avs]
+    sizes = [(64, 48), (96, 96), (33, 70), (128, 64)]
+    cams = _cams(12, 3)
+    reqs = [(ids[i % 3], cams[i], sizes[i % 4]) for i in range(12)]
+    # alone: one request at a time
+    alone = []
+    for aid, cam, (w, h) in reqs:
+        tk = srv.submit_raw(T.Server.request(aid, cam, float(w), w, h, T_NEAR, T_FAR, DT))
+        out = torch.empty((h * w, 4), dtype=torch.float32, device=DEV)
+        st, _ = srv.wait(tk, 10000.0, out)
+        assert st == B.MVP_OK
+        alone.append(out)
+    # in the mix: all submitted back to back, polled out of order
+    tks = [srv.submit_raw(T.Server.request(aid, cam, float(w), w, h, T_NEAR, T_FAR, DT)) for aid, cam, (w, h) in reqs]
+    mix = [torch.empty((h * w, 4), dtype=torch.float32, device=DEV) for _, _, (w, h) in reqs]
+    for j in reversed(range(len(tks))):
+        st, _ = srv.wait(tks[j], 10000.0, mix[j])
+        assert st == B.MVP_OK
+    stats = srv.stats()
+    assert stats["device_status"] == 0
+    assert stats["max_in_flight"] >= 4  # the burst was in flight together
+    for (aid, cam, (w, h)), a, m in zip(reqs, alone, mix):
+        assert torch.equal(a, m), "alone and in the mix differ"
+        ref = _reference(ctx, avs[aid], cam, float(w), w, h)
+        assert (a - ref).abs().max().item() <= 1e-5
+        assert a[:, 3].max().item() > 0  # the avatar is in view
+    srv.close()
+
+
+def test_admission_respects_budget_and_frees_memory():
+    torch.cuda.set_device(0)
+    ctx = T.Context(0)
+    av = _avatars(ctx)[0]
+    probe = T.Server(ctx, hbm_budget=1 << 30)
+    probe.register(*av)
+    resident = probe.stats()["resident_bytes"]
+    probe.close()
+    w = h = 64
+    img = w * h * 16
+    srv = T.Server(ctx, hbm_budget=resident + 2 * img + 100, max_slots=8)
+    aid = srv.register(*av)
+    cams = _cams(6, 7)
+    tks = [srv.submit_raw(T.Server.request(aid, c, 64.0, w, h, T_NEAR, T_FAR, DT)) for c in cams]
+    st = srv.stats()
+    assert st["in_flight"] <= 2 and st["pending"] >= 4
+    outs = []
+    for tk in tks:
+        out = torch.empty((h * w, 4), dtype=torch.float32, device=DEV)
+        s_, _ = srv.wait(tk, 10000.0, out)
+        assert s_ == B.MVP_OK
+        outs.append(out)
+    st = srv.stats()
+    assert st["max_in_flight"] <= 2 and st["completed"] == 6 and st["in_flight_bytes"] == 0
+    for c, o in zip(cams, outs):
+        assert (o - _reference(ctx, av, c, 64.0, w, h)).abs().max().item() <= 1e-5
+    # a request whose image alone exceeds the budget is refused
+    with pytest.raises(B.MVPError) as ei:
+        srv.submit_raw(T.Server.request(aid, cams[0], 64.0, 512, 512, T_NEAR, T_FAR, DT))
+    assert ei.value.status == B.MVP_ERR_CAPACITY
+    srv.close()
+
+
+def test_wait_timeout_unknown_ticket_and_bad_avatar():
+    torch.cuda.set_device(0)
+    ctx = T.Context(0)
+    av = _avatars(ctx)[0]
+    probe = T.Server(ctx, hbm_budget=1 << 30)
+    probe.register(*av)
+    resident = probe.stats()["resident_bytes"]
+    probe.close()
+    w = h = 32
+    srv = T.Server(ctx, hbm_budget=resident + w * h * 16 + 100, max_slots=4)
+    aid = srv.register(*av)
+    cams = _cams(2, 9)
+    t1 = srv.submit_raw(T.Server.request(aid, cams[0], 32.0, w, h, T_NEAR, T_FAR, DT))
+    t2 = srv.submit_raw(T.Server.request(aid, cams[1], 32.0, w, h, T_NEAR, T_FAR, DT))
+    # t2 cannot be admitted until t1 is collected: a wait on it runs out
+    st, _ = srv.wait(t2, 5.0)
+    assert st == B.MVP_ERR_TIMEOUT
+    st, _ = srv.wait(t1, 10000.0)
+    assert st == B.MVP_OK
+    st, _ = srv.wait(t2, 10000.0)
+    assert st == B.MVP_OK
+    with pytest.raises(B.MVPError):
+        srv.poll(12345)
+    with pytest.raises(B.MVPError) as ei:
+        srv.submit_raw(T.Server.request(7, cams[0], 32.0, w, h, T_NEAR, T_FAR, DT))
+    assert ei.value.status == B.MVP_ERR_INVALID_ARG
+    srv.close()
