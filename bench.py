@@ -43,6 +43,21 @@ def _dist():
     return ws, rank
 
 
+def aggregate(ms_local: float, rays_local: int, world: int, device=None) -> tuple[float, float]:
+    """Weak scaling over ranks: every rank renders its own frame; the job's step time
+    is the slowest rank's, and the value counts the rays of all ranks.
+    Returns (ms_per_step, Mrays/s). Collective only when world > 1."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        tt = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    return ms, world * rays_local / (ms * 1e-3) / 1e6
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -258,6 +273,92 @@ def _traffic(kernel_key: str):
     return None
 
 
+def _serving(torch, T, synthetic, rates, n_req, seed=0):
+    """Poisson arrivals over 8 resident BF16 avatars (512x32^3 ... 32768x8^3), random
+    cameras on the radius-3 sphere, resolutions {256x256, 512x512, 667x1024}; served
+    with continuous batching (mvp_serve_*) and, on the same trace, one request at a
+    time with FP32 payloads (mvp_camera_rays + mvp_raymarch_fwd, synchronised)."""
+    import time as _t
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx = T.Context(dev.index)
+    av_bf16, av_f32, bvhs = [], [], []
+    for i in range(len(synthetic.AVATARS)):
+        sc = synthetic.make_avatar(i, seed)
+        t = torch.from_numpy(sc.t).to(dev)
+        q = torch.from_numpy(sc.q).to(dev)
+        s = torch.from_numpy(sc.s).to(dev)
+        p32 = torch.from_numpy(sc.payload).to(dev)
+        av_f32.append((t, q, s, p32))
+        av_bf16.append((t, q, s, T.pack_payload(ctx, p32, torch.bfloat16)))
+        bvh = T.BVH(ctx)
+        bvh.build(T.prims_struct(t, q, s, p32))
+        bvhs.append(bvh)
+    srv = T.Server(ctx, hbm_budget=100 * 10**9, max_slots=64, arena_bytes=2 << 30)
+    ids = [srv.register(*a) for a in av_bf16]
+    resident = srv.stats()["resident_bytes"]
+    out_buf = torch.empty((1024 * 667, 4), dtype=torch.float32, device=dev)
+    results = {}
+    for rate in rates:
+        rng = np.random.default_rng(seed + int(rate))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        reqs = []
+        for j in range(n_req):
+            a = int(rng.integers(0, len(ids)))
+            w, h = synthetic.SERVE_RESOLUTIONS[int(rng.integers(0, 3))]
+            cam = synthetic.random_camera(rng, 3.0, w, h, float(max(w, h)))
+            reqs.append((a, cam, w, h))
+        # warm-up: a few requests so kernels and arenas are resident
+        for a, cam, w, h in reqs[:4]:
+            tk = srv.submit_raw(T.Server.request(ids[a], cam.matrix34(), cam.focal, w, h, 1.0, 5.0, 0.005))
+            srv.wait(tk, 60000.0)
+        # continuous batching
+        lat, pend = [], {}
+        rays = sum(w * h for _, _, w, h in reqs)
+        t0 = _t.perf_counter()
+        j = 0
+        while j < n_req or pend:
+            now = _t.perf_counter() - t0
+            while j < n_req and arrivals[j] <= now:
+                a, cam, w, h = reqs[j]
+                pend[srv.submit_raw(T.Server.request(ids[a], cam.matrix34(), cam.focal, w, h, 1.0, 5.0, 0.005))] = j
+                j += 1
+            for tk in list(pend):
+                st, ms = srv.poll(tk)
+                if st == 0:
+                    lat.append(ms)
+                    del pend[tk]
+        wall = _t.perf_counter() - t0
+        st_ = srv.stats()
+        # one request at a time, FP32 payloads, same trace
+        lat1 = []
+        t0 = _t.perf_counter()
+        for k, (a, cam, w, h) in enumerate(reqs):
+            while _t.perf_counter() - t0 < arrivals[k]:
+                pass
+            tt, qq, ss, pp = av_f32[a]
+            prims = T.prims_struct(tt, qq, ss, pp)
+            o, d = T.camera_rays(ctx, cam.matrix34(), cam.focal, w, h)
+            rs = T.rays_struct(o, d, t_near=1.0, t_far=5.0, dt=0.005, width=w, height=h)
+            T.raymarch_fwd(ctx, prims, bvhs[a], rs, out=out_buf[: w * h])
+            torch.cuda.current_stream().synchronize()
+            lat1.append((_t.perf_counter() - t0 - arrivals[k]) * 1e3)
+        wall1 = _t.perf_counter() - t0
+        ctx.sync()
+        results[f"{rate}_req_per_s"] = {
+            "requests": n_req, "p50_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3), "mrays_per_s": round(rays / wall / 1e6, 2),
+            "max_in_flight": int(st_["max_in_flight"]), "device_status": int(st_["device_status"]),
+            "one_at_a_time_f32": {"p50_ms": round(float(np.percentile(lat1, 50)), 3),
+                                  "p99_ms": round(float(np.percentile(lat1, 99)), 3),
+                                  "mrays_per_s": round(rays / wall1 / 1e6, 2)}}
+    srv.close()
+    return {"avatars": [f"{n}x{M}^3" for n, M, _ in synthetic.AVATARS], "payload": "bf16",
+            "resident_bytes": int(resident), "hbm_budget": 100 * 10**9,
+            "resolutions": ["256x256", "512x512", "667x1024"], "latency": "host time from submit to completion seen",
+            "rates": results}
+
+
 def run_gpu(args):
     import torch
 
@@ -283,18 +384,11 @@ def run_gpu(args):
     with ClockSampler(local) as clk:
         durs = _time_steps(torch, step, args.steps, args.warmup, flush, time_march=True)
     info["ctx"].sync()
-    ms = float(np.mean(durs))
-    if ws > 1:
-        import torch.distributed as dist
-
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms, value = aggregate(float(np.mean(durs)), n_rays, ws, dev)
     march_ms = float(np.mean([a.elapsed_time(b) for a, b in info["ev"]["march"]]))
     # evaluations of one frame (the work count of the roofline)
     n_eval = int(T.raymarch_count(info["ctx"], info["prims"], info["bvh"], info["rs"]).sum().item())
     info["ctx"].sync()
-    value = ws * n_rays / (ms * 1e-3) / 1e6
 
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s (FMA = 2)
@@ -350,6 +444,10 @@ def run_gpu(args):
         if variants.get("fwd_bf16"):
             variants["bf16_over_f32"] = round(variants["fwd_bf16"]["value"] / value, 3)
         result["variants"] = variants
+        if args.serving_requests > 0:
+            rates = [float(r) for r in args.serving_rates.split(",")]
+            result["serving"] = _serving(torch, T, synthetic, rates, args.serving_requests)
+            torch.cuda.empty_cache()
         if not args.no_cpu:
             result["cpu_baseline"] = _cpu_baseline(args.cpu_seconds)
     if ws > 1:
@@ -425,6 +523,9 @@ def main():
     ap.add_argument("--quick", action="store_true", help="headline figure only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serving-requests", type=int, default=400, help="requests per arrival rate (0: skip)")
+    ap.add_argument("--serving-rates", default="50,200,400,1600", help="Poisson arrival rates, requests/s")
+    ap.add_argument("--serving-only", action="store_true", help="run only the serving measurement")
     ap.add_argument("--profile", action="store_true", help="render --frames frames of --workload, no timing")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
@@ -433,6 +534,16 @@ def main():
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
+        return
+    if args.serving_only:
+        import torch
+
+        import synthetic
+        from paper_2103_01954_gb300 import torch_ops as T
+
+        torch.cuda.set_device(0)
+        rates = [float(r) for r in args.serving_rates.split(",")]
+        print(json.dumps({"serving": _serving(torch, T, synthetic, rates, args.serving_requests)}))
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -46,7 +46,7 @@ class mvp_request(ctypes.Structure):
 class mvp_serve_info(ctypes.Structure):
     _fields_ = [("pending", c_int64), ("in_flight", c_int64), ("max_in_flight", c_int64), ("completed", c_int64),
                 ("resident_bytes", c_int64), ("in_flight_bytes", c_int64), ("grid_blocks", c_int32),
-                ("avatars", c_int32), ("device_status", c_int32), ("reserved", c_int32)]
+                ("avatars", c_int32), ("device_status", c_int32), ("reserved", c_int32), ("batches", c_int64)]
 
 
 class MVPError(RuntimeError):

@@ -1,26 +1,24 @@
 // serve.cu -- continuous batching of render requests (different avatars, cameras
-// and resolutions) through one persistent kernel.
+// and resolutions), each batch in one persistent kernel launch.
 //
-// Device side. Every admitted request is cut into warp tiles of 8x4 pixels that are
-// numbered consecutively in one global, ever-growing tile sequence: request j owns
-// tiles [base_j, base_j + n_j). The host publishes a request by writing its
-// descriptor into a ring slot and then raising `published` (release). Worker warps
-// claim the next tile number from a device counter (never past `published`), find
-// the request that owns it, generate the tile's camera rays and march the tile with
-// the same code as mvp_raymarch_fwd (march_tile). A warp that finds no unclaimed
-// published tile returns: nothing on the device ever waits. The warp that finishes
-// a request's last tile resets the slot's tile counter and publishes the request's
-// completion (release, system scope).
+// Device side. A batch is a list of admitted requests; each request is cut into
+// warp tiles of 8x4 pixels numbered consecutively across the batch. The batch's
+// grid (one CTA set per SM) has every warp claim tile numbers from the batch's own
+// counter, find the owning request (its descriptor is copied once into shared
+// memory), generate the tile's pinhole rays and march it with the same code as
+// mvp_raymarch_fwd (march_tile). A warp past the batch's last tile returns: nothing
+// on the device ever waits. The warp that finishes a request's last tile publishes
+// its completion to mapped host memory (system-scope release), so a small request
+// completes without waiting for the rest of its batch.
 //
-// Host side. Each submit launches one worker grid (one CTA set per SM) on the
-// server's work stream after publishing; a grid that starts after earlier grids
-// have drained the queue exits at once, and a request published while a grid runs
-// is picked up by that grid's warps as they free up, so requests of different sizes
-// overlap on the device. Admission: a request needs a free ring slot and its image
-// (W*H*16 bytes) must fit both the HBM budget (resident avatars + images in flight)
-// and the server's image arena; otherwise it waits in a FIFO and is admitted by a
-// later submit or poll, as slots and memory free up. A request larger than the
-// budget itself is refused with MVP_ERR_CAPACITY.
+// Host side. Admission: a request needs a free slot and its image (W*H*16 bytes)
+// must fit the HBM budget (resident avatars + images in flight) and the server's
+// image arena; otherwise it waits in a FIFO and is admitted by a later submit or
+// poll as slots and memory free up. Admitted requests are launched as a batch on
+// one of several streams as soon as one is idle; requests that arrive while batches
+// run form the next batch on another stream, whose blocks start as SMs free up, so
+// requests overlap on the device. A request larger than the budget is refused
+// (MVP_ERR_CAPACITY).
 #include <math.h>
 #include <string.h>
 
@@ -37,14 +35,15 @@
 namespace mvp {
 
 constexpr int SERVE_CAP = MARCH_CAP;
+constexpr int SERVE_STREAMS = 4;  // batches that may run at once
 
-// Request descriptor, in mapped pinned host memory: written by the host, read by
-// the device. `seq` is written last (release) and read first (acquire).
-struct ReqDesc {
-  unsigned long long seq;
-  unsigned long long base;  // first tile of the request in the global sequence
+// One request of a batch (device memory, copied in before the batch's launch).
+struct BatchReq {
+  unsigned long long seq;  // request sequence number
+  int slot;                // completion record index
+  int tile_begin;          // first tile of the request within the batch
   int n_tiles;
-  int n_prims, M, dtype, n_steps, width, height, pad0;
+  int n_prims, M, dtype, n_steps, width, height;
   const void *payload;
   const Node *nodes;
   const Pose *pose;
@@ -53,27 +52,15 @@ struct ReqDesc {
   float c2w[12];
   float focal, t_near, t_far, dt, stop_T;
   float bg[3];
+  int pad;
 };
 
-// Completion record, written by the device, read by the host.
+// Completion record of a slot (mapped host memory): written by the device.
 struct ReqDone {
   unsigned long long seq_done;  // 1 + sequence number of the request completed in this slot (0: none)
   unsigned long long t_start_ns, t_end_ns;
   unsigned long long pad;
 };
-
-// Shared host/device state (mapped pinned memory).
-struct ServeShared {
-  unsigned long long published;  // tiles published so far
-  unsigned long long oldest;     // no request before this sequence number is incomplete
-  unsigned long long pad[6];
-};
-
-__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long *p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
 
 __device__ __forceinline__ void st_release_sys(unsigned long long *p, unsigned long long v) {
   asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -85,125 +72,83 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 
-struct ServeArgs {
-  ServeShared *shared;     // mapped
-  ReqDesc *ring;           // mapped, ring_size entries
-  ReqDone *done;           // mapped, ring_size entries
-  unsigned long long *claimed;  // device: next tile number to hand out
-  unsigned int *tiles_done;     // device: finished tiles per slot
-  int ring_size;
-  int total_warps;
+struct BatchArgs {
+  const BatchReq *reqs;     // device, n_req entries
+  int n_req;
+  int total_tiles;
+  unsigned int *claimed;    // device, zeroed before the launch
+  unsigned int *tiles_done; // device, n_req entries, zeroed before the launch
+  ReqDone *done;            // mapped host memory, indexed by slot
   int *status;
 };
-
-// Next published, unclaimed tile number, or -1 if there is none (lane 0 decides).
-__device__ __forceinline__ long long claim_tile(const ServeArgs &A) {
-  long long t = -1;
-  if ((threadIdx.x & 31) == 0) {
-    for (int it = 0; it < (1 << 20); ++it) {
-      const unsigned long long p = ld_acquire_sys(&A.shared->published);
-      const unsigned long long c = *reinterpret_cast<volatile unsigned long long *>(A.claimed);
-      if (c >= p) break;
-      if (p - c > (unsigned long long)A.total_warps) {
-        // more unclaimed tiles than warps: a plain increment cannot pass `published`
-        t = (long long)atomicAdd(A.claimed, 1ull);
-        break;
-      }
-      if (atomicCAS(A.claimed, c, c + 1) == c) {
-        t = (long long)c;
-        break;
-      }
-      if (it == (1 << 20) - 1) atomicOr(A.status, STATUS_DEVICE);
-    }
-  }
-  return __shfl_sync(FULL, t, 0);
-}
 
 template <int DT>
 __device__ __noinline__ void serve_tile(TileShared<SERVE_CAP> &sh, const MarchArgs &a, const LaneRay &L) {
   march_tile<DT, SERVE_CAP, false, 0>(sh, a, L);
 }
 
-__global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_serve(ServeArgs A) {
+__global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_serve(BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   TileShared<SERVE_CAP> &sh = reinterpret_cast<TileShared<SERVE_CAP> *>(smem_raw)[warp];
-  unsigned long long cursor = 0;
+  BatchReq &D = reinterpret_cast<BatchReq *>(smem_raw + sizeof(TileShared<SERVE_CAP>) * TILE_WARPS)[warp];
+  int cur = -1, c_begin = 0, c_n = 0;
   while (true) {
-    const long long t = claim_tile(A);
-    if (t < 0) return;
-    // every request before `oldest` is complete, and the owner of t is not, so the
-    // owner is at most (requests in flight) ahead of this bound
-    const unsigned long long lb = ld_acquire_sys(&A.shared->oldest);
-    if (cursor < lb) cursor = lb;
-    // find the request owning tile t: scan forward from the cursor (tile numbers a
-    // warp claims only grow, and every request before the owner is published)
-    int slot = -1;
-    unsigned long long base = 0;
-    for (int it = 0; it < 4 * A.ring_size + 64; ++it) {
-      const int s = (int)(cursor % (unsigned long long)A.ring_size);
-      const unsigned long long seq = ld_acquire_sys(&A.ring[s].seq);
-      if (seq != cursor) {  // recycled: request `cursor` completed, so it cannot own t
-        ++cursor;
-        continue;
+    unsigned int tl = 0;
+    if (lane == 0) tl = atomicAdd(A.claimed, 1u);
+    const int t = (int)__shfl_sync(FULL, tl, 0);
+    if (t >= A.total_tiles) return;
+    if (cur < 0 || t < c_begin || t >= c_begin + c_n) {
+      // owning request: the last one whose first tile is <= t (requests are in tile order)
+      int lo = 0, hi = A.n_req - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&A.reqs[mid].tile_begin) <= t) lo = mid; else hi = mid - 1;
       }
-      const volatile ReqDesc *D = &A.ring[s];
-      const unsigned long long b = D->base;
-      const int n = D->n_tiles;
-      if (ld_acquire_sys(&A.ring[s].seq) != cursor) {
-        ++cursor;
-        continue;
-      }
-      if ((unsigned long long)t < b + (unsigned long long)n) {
-        slot = s;
-        base = b;
-        break;
-      }
-      ++cursor;
+      cur = lo;
+      constexpr int W = (int)(sizeof(BatchReq) / 4);
+      static_assert(sizeof(BatchReq) % 4 == 0 && W <= 64, "descriptor copy");
+      const unsigned int *src = reinterpret_cast<const unsigned int *>(&A.reqs[cur]);
+      unsigned int *dst = reinterpret_cast<unsigned int *>(&D);
+      __syncwarp();
+      for (int w = lane; w < W; w += 32) dst[w] = __ldg(src + w);
+      __syncwarp();
+      c_begin = D.tile_begin;
+      c_n = D.n_tiles;
     }
-    if (slot < 0) {  // inconsistent queue state: report and stop this warp
-      if (lane == 0) atomicOr(A.status, STATUS_DEVICE);
-      return;
-    }
-    const volatile ReqDesc *D = &A.ring[slot];
-    if (lane == 0 && (unsigned long long)t == base) A.done[slot].t_start_ns = globaltimer();
+    if (lane == 0 && t == c_begin) A.done[D.slot].t_start_ns = globaltimer();
     MarchArgs a;
-    a.n_prims = D->n_prims;
-    a.M = D->M;
-    a.dtype = D->dtype;
-    a.payload = D->payload;
-    a.nodes = D->nodes;
-    a.pose = D->pose;
-    a.xf = D->xf;
-    const int width = D->width, height = D->height;
+    a.n_prims = D.n_prims;
+    a.M = D.M;
+    a.dtype = D.dtype;
+    a.payload = D.payload;
+    a.nodes = D.nodes;
+    a.pose = D.pose;
+    a.xf = D.xf;
+    const int width = D.width, height = D.height;
     a.geom.n_rays = (int64_t)width * height;
     a.geom.width = width;
     a.geom.height = height;
-    a.geom.n_warp_tiles = D->n_tiles;
+    a.geom.n_warp_tiles = D.n_tiles;
     a.o = a.d = nullptr;
-    a.t_near = D->t_near;
-    a.t_far = D->t_far;
-    a.dt = D->dt;
-    a.stop_T = D->stop_T;
-    a.bg[0] = D->bg[0];
-    a.bg[1] = D->bg[1];
-    a.bg[2] = D->bg[2];
-    a.n_steps = D->n_steps;
-    a.out = D->out;
+    a.t_near = D.t_near;
+    a.t_far = D.t_far;
+    a.dt = D.dt;
+    a.stop_T = D.stop_T;
+    a.bg[0] = D.bg[0];
+    a.bg[1] = D.bg[1];
+    a.bg[2] = D.bg[2];
+    a.n_steps = D.n_steps;
+    a.out = D.out;
     a.saved = nullptr;
     a.n_eval = nullptr;
     a.status = A.status;
-    float m[12];
-#pragma unroll
-    for (int i = 0; i < 12; ++i) m[i] = D->c2w[i];
-    const float focal = D->focal;
-    // the tile's rays
     LaneRay L;
-    const int64_t r = tile_ray(a.geom, t - (long long)base, lane);
+    const int64_t r = tile_ray(a.geom, (int64_t)(t - c_begin), lane);
     L.r = r;
     if (r >= 0) {
       const int row = (int)(r / width), col = (int)(r - (int64_t)row * width);
-      camera_ray(m, focal, width, height, row, col, L.o, L.d);
+      camera_ray(D.c2w, D.focal, width, height, row, col, L.o, L.d);
     } else {
 #pragma unroll
       for (int j = 0; j < 3; ++j) L.o[j] = L.d[j] = 0.0f;
@@ -218,13 +163,12 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_serve(ServeArgs A) {
     __syncwarp();
     if (lane == 0) {
       __threadfence();  // this tile's pixels are visible before it is counted
-      const unsigned int fin = atomicAdd(&A.tiles_done[slot], 1u);
-      if (fin + 1 == (unsigned int)D->n_tiles) {
+      const unsigned int fin = atomicAdd(&A.tiles_done[cur], 1u);
+      if (fin + 1 == (unsigned int)c_n) {
         __threadfence();
-        A.tiles_done[slot] = 0;  // the slot is idle until the host reuses it
-        A.done[slot].t_end_ns = globaltimer();
+        A.done[D.slot].t_end_ns = globaltimer();
         __threadfence_system();
-        st_release_sys(&A.done[slot].seq_done, cursor + 1);
+        st_release_sys(&A.done[D.slot].seq_done, D.seq + 1);
       }
     }
     __syncwarp();
@@ -234,7 +178,6 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_serve(ServeArgs A) {
 }  // namespace mvp
 
 // ============================================================================ host
-
 namespace {
 
 using clock_type = std::chrono::steady_clock;
@@ -255,7 +198,9 @@ struct InFlight {
   uint64_t seq = 0;
   int slot = -1;
   size_t off = 0, bytes = 0;
+  mvp_request req;
   clock_type::time_point submit;
+  bool launched = false;
 };
 
 // First-fit allocator over the image arena (host bookkeeping only).
@@ -298,34 +243,42 @@ struct Arena {
   }
 };
 
+// Per-stream batch buffers: the batch table is staged in pinned memory and copied to
+// the device on the stream before the launch; the stream is reused only after its
+// previous batch (and that copy) finished.
+struct Lane {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  bool busy = false;
+  mvp::BatchReq *h_reqs = nullptr;  // pinned staging
+  mvp::BatchReq *d_reqs = nullptr;
+  unsigned int *d_counters = nullptr;  // [0] claimed, [1..] tiles done per request
+};
+
 }  // namespace
 
 struct mvp_server {
   int device = 0;
   size_t budget = 0;
-  int ring = 0;
+  int slots = 0;
   std::mutex mu;
   std::vector<Avatar> avatars;
   size_t resident = 0;
   size_t inflight_bytes = 0;
   Arena arena;
   char *arena_base = nullptr;
-  mvp::ServeShared *h_shared = nullptr, *d_shared = nullptr;
-  mvp::ReqDesc *h_ring = nullptr, *d_ring = nullptr;
-  mvp::ReqDone *h_done = nullptr, *d_done = nullptr;
-  unsigned long long *d_claimed = nullptr;
-  unsigned int *d_tiles_done = nullptr;
+  mvp::ReqDone *h_done = nullptr, *d_done = nullptr;  // mapped
   int *d_status = nullptr;
-  cudaStream_t work = nullptr, copy = nullptr;
+  Lane lanes[mvp::SERVE_STREAMS];
+  cudaStream_t copy = nullptr;
   int grid = 0;
   size_t smem = 0;
-  uint64_t next_seq = 0, next_ticket = 1, published = 0;
+  uint64_t next_seq = 0, next_ticket = 1;
   std::vector<bool> slot_busy;
-  std::vector<uint64_t> slot_seq;
   std::deque<Pending> pending;
-  std::map<uint64_t, InFlight> inflight;
+  std::map<uint64_t, InFlight> inflight;  // ticket -> request (admitted)
   size_t max_inflight_seen = 0;
-  uint64_t completed = 0;
+  uint64_t completed = 0, batches = 0;
 };
 
 namespace {
@@ -337,100 +290,116 @@ mvp_status serve_fail(mvp_status s, const char *msg) {
 
 size_t image_bytes(const mvp_request &r) { return (size_t)r.width * (size_t)r.height * 4 * sizeof(float); }
 
-int64_t warp_tiles(int w, int h) { return (int64_t)((w + 15) / 16) * ((h + 7) / 8) * 4; }
+int warp_tiles(int w, int h) { return ((w + 15) / 16) * ((h + 7) / 8) * 4; }
 
-// Oldest incomplete request (lower bound for the device's scans).
-uint64_t oldest_incomplete(mvp_server *S) {
-  uint64_t o = S->next_seq;
-  for (auto &kv : S->inflight) {
-    const unsigned long long v = __atomic_load_n(&S->h_done[kv.second.slot].seq_done, __ATOMIC_ACQUIRE);
-    if (v != kv.second.seq + 1) o = kv.second.seq < o ? kv.second.seq : o;
-  }
-  return o;
-}
-
-// Admit pending requests in FIFO order while a slot, budget and arena space allow;
-// launch one worker grid if anything was published. Called with S->mu held.
+// Admit pending requests in FIFO order while a slot, budget and arena space allow,
+// then launch the admitted, not yet launched requests as one batch on an idle
+// stream. Called with S->mu held.
 mvp_status pump(mvp_server *S) {
-  bool launched = false;
   while (!S->pending.empty()) {
     Pending &p = S->pending.front();
     const size_t bytes = image_bytes(p.req);
-    const int slot = (int)(S->next_seq % (uint64_t)S->ring);
-    if (S->slot_busy[slot]) break;
+    int slot = -1;
+    for (int i = 0; i < S->slots; ++i)
+      if (!S->slot_busy[i]) {
+        slot = i;
+        break;
+      }
+    if (slot < 0) break;
     if (S->resident + S->inflight_bytes + bytes > S->budget) break;
     size_t off = 0;
     if (!S->arena.alloc(bytes, off)) break;
-    const Avatar &A = S->avatars[p.req.avatar];
-    const mvp_request &q = p.req;
-    mvp::ReqDesc &D = S->h_ring[slot];
-    const uint64_t seq = S->next_seq++;
-    const int64_t nt = warp_tiles(q.width, q.height);
-    D.base = S->published;
-    D.n_tiles = (int)nt;
-    D.n_prims = A.prims.n;
-    D.M = A.prims.M;
-    D.dtype = A.prims.dtype;
-    D.n_steps = (int)mvp_num_steps(q.t_near, q.t_far, q.dt);
-    D.width = q.width;
-    D.height = q.height;
-    D.payload = A.prims.payload;
-    D.nodes = A.bvh.nodes;
-    D.pose = A.bvh.pose;
-    D.xf = A.bvh.xf;
-    D.out = reinterpret_cast<float *>(S->arena_base + off);
-    memcpy(D.c2w, q.c2w, sizeof(D.c2w));
-    D.focal = q.focal;
-    D.t_near = q.t_near;
-    D.t_far = q.t_far;
-    D.dt = q.dt;
-    D.stop_T = (float)(1.0 - (double)q.eps_early);
-    memcpy(D.bg, q.bg, sizeof(D.bg));
-    // the completion record holds seq + 1 once done (0: nothing completed yet)
-    __atomic_store_n(&S->h_done[slot].seq_done, 0ull, __ATOMIC_RELAXED);
-    __atomic_store_n(&D.seq, (unsigned long long)seq, __ATOMIC_RELEASE);
-    S->published += (uint64_t)nt;
-    S->slot_busy[slot] = true;
-    S->slot_seq[slot] = seq;
     InFlight f;
-    f.seq = seq;
+    f.seq = S->next_seq++;
     f.slot = slot;
     f.off = off;
     f.bytes = bytes;
+    f.req = p.req;
     f.submit = p.submit;
+    __atomic_store_n(&S->h_done[slot].seq_done, 0ull, __ATOMIC_RELEASE);
+    S->slot_busy[slot] = true;
     S->inflight[p.ticket] = f;
-    // the scan bound first (it includes this request), then the tiles (release)
-    __atomic_store_n(&S->h_shared->oldest, (unsigned long long)oldest_incomplete(S), __ATOMIC_RELEASE);
-    __atomic_store_n(&S->h_shared->published, (unsigned long long)S->published, __ATOMIC_RELEASE);
     S->inflight_bytes += bytes;
     if (S->inflight.size() > S->max_inflight_seen) S->max_inflight_seen = S->inflight.size();
     S->pending.pop_front();
-    launched = true;
   }
-  if (launched) {
-    mvp::ServeArgs a;
-    a.shared = S->d_shared;
-    a.ring = S->d_ring;
-    a.done = S->d_done;
-    a.claimed = S->d_claimed;
-    a.tiles_done = S->d_tiles_done;
-    a.ring_size = S->ring;
-    a.total_warps = S->grid * mvp::TILE_WARPS;
-    a.status = S->d_status;
-    mvp::k_serve<<<S->grid, mvp::TILE_WARPS * 32, S->smem, S->work>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return serve_fail(MVP_ERR_CUDA, cudaGetErrorString(e));
+  // anything admitted but not launched?
+  bool any = false;
+  for (auto &kv : S->inflight)
+    if (!kv.second.launched) {
+      any = true;
+      break;
+    }
+  if (!any) return MVP_OK;
+  // an idle stream (its previous batch finished)
+  Lane *L = nullptr;
+  for (int i = 0; i < mvp::SERVE_STREAMS; ++i) {
+    Lane &c = S->lanes[i];
+    if (c.busy && cudaEventQuery(c.done) == cudaSuccess) c.busy = false;
+    if (!c.busy && !L) L = &c;
   }
+  if (!L) return MVP_OK;  // launched when a stream frees up (next submit or poll)
+  int n = 0, tiles = 0;
+  for (auto &kv : S->inflight) {
+    InFlight &f = kv.second;
+    if (f.launched) continue;
+    const mvp_request &q = f.req;
+    const Avatar &A = S->avatars[q.avatar];
+    mvp::BatchReq &B = L->h_reqs[n++];
+    memset(&B, 0, sizeof(B));
+    B.seq = f.seq;
+    B.slot = f.slot;
+    B.tile_begin = tiles;
+    B.n_tiles = warp_tiles(q.width, q.height);
+    B.n_prims = A.prims.n;
+    B.M = A.prims.M;
+    B.dtype = A.prims.dtype;
+    B.n_steps = (int)mvp_num_steps(q.t_near, q.t_far, q.dt);
+    B.width = q.width;
+    B.height = q.height;
+    B.payload = A.prims.payload;
+    B.nodes = A.bvh.nodes;
+    B.pose = A.bvh.pose;
+    B.xf = A.bvh.xf;
+    B.out = reinterpret_cast<float *>(S->arena_base + f.off);
+    memcpy(B.c2w, q.c2w, sizeof(B.c2w));
+    B.focal = q.focal;
+    B.t_near = q.t_near;
+    B.t_far = q.t_far;
+    B.dt = q.dt;
+    B.stop_T = (float)(1.0 - (double)q.eps_early);
+    memcpy(B.bg, q.bg, sizeof(B.bg));
+    tiles += B.n_tiles;
+    f.launched = true;
+  }
+  cudaError_t e = cudaMemcpyAsync(L->d_reqs, L->h_reqs, sizeof(mvp::BatchReq) * n, cudaMemcpyHostToDevice, L->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(L->d_counters, 0, sizeof(unsigned int) * (n + 1), L->stream);
+  if (e != cudaSuccess) return serve_fail(MVP_ERR_CUDA, cudaGetErrorString(e));
+  mvp::BatchArgs a;
+  a.reqs = L->d_reqs;
+  a.n_req = n;
+  a.total_tiles = tiles;
+  a.claimed = L->d_counters;
+  a.tiles_done = L->d_counters + 1;
+  a.done = S->d_done;
+  a.status = S->d_status;
+  int grid = S->grid;
+  const int need = (tiles + mvp::TILE_WARPS - 1) / mvp::TILE_WARPS;
+  if (need < grid) grid = need;
+  mvp::k_serve<<<grid, mvp::TILE_WARPS * 32, S->smem, L->stream>>>(a);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaEventRecord(L->done, L->stream);
+  if (e != cudaSuccess) return serve_fail(MVP_ERR_CUDA, cudaGetErrorString(e));
+  L->busy = true;
+  S->batches++;
   return MVP_OK;
 }
 
-}  // namespace
-
-// The completion record of the slot holds seq + 1 once the request is done.
-static bool is_done(mvp_server *S, const InFlight &f) {
-  unsigned long long v = __atomic_load_n(&S->h_done[f.slot].seq_done, __ATOMIC_ACQUIRE);
-  return v == f.seq + 1;
+bool is_done(mvp_server *S, const InFlight &f) {
+  return __atomic_load_n(&S->h_done[f.slot].seq_done, __ATOMIC_ACQUIRE) == f.seq + 1;
 }
+
+}  // namespace
 
 extern "C" {
 
@@ -446,9 +415,8 @@ mvp_status mvp_serve_create(mvp_ctx *ctx, size_t hbm_budget, int32_t max_slots, 
   if (!S) return serve_fail(MVP_ERR_OOM, "host allocation");
   S->device = dev;
   S->budget = hbm_budget;
-  S->ring = max_slots;
+  S->slots = max_slots;
   S->slot_busy.assign(max_slots, false);
-  S->slot_seq.assign(max_slots, 0);
   size_t arena = arena_bytes ? arena_bytes : hbm_budget;
   if (arena > hbm_budget) arena = hbm_budget;
   cudaError_t e = cudaSuccess;
@@ -458,29 +426,28 @@ mvp_status mvp_serve_create(mvp_ctx *ctx, size_t hbm_budget, int32_t max_slots, 
   };
   if ((e = cudaMalloc(&S->arena_base, arena)) != cudaSuccess) return bail("image arena allocation");
   S->arena.init(arena);
-  size_t host_bytes = sizeof(mvp::ServeShared) + sizeof(mvp::ReqDesc) * max_slots + sizeof(mvp::ReqDone) * max_slots;
   char *h = nullptr;
-  if ((e = cudaHostAlloc(&h, host_bytes, cudaHostAllocMapped)) != cudaSuccess) return bail("mapped host memory");
-  memset(h, 0, host_bytes);
-  S->h_shared = reinterpret_cast<mvp::ServeShared *>(h);
-  S->h_ring = reinterpret_cast<mvp::ReqDesc *>(h + sizeof(mvp::ServeShared));
-  S->h_done = reinterpret_cast<mvp::ReqDone *>(h + sizeof(mvp::ServeShared) + sizeof(mvp::ReqDesc) * max_slots);
-  for (int i = 0; i < max_slots; ++i) S->h_ring[i].seq = ~0ull;
+  if ((e = cudaHostAlloc(&h, sizeof(mvp::ReqDone) * max_slots, cudaHostAllocMapped)) != cudaSuccess)
+    return bail("mapped host memory");
+  memset(h, 0, sizeof(mvp::ReqDone) * max_slots);
+  S->h_done = reinterpret_cast<mvp::ReqDone *>(h);
   char *d = nullptr;
   if ((e = cudaHostGetDevicePointer(&d, h, 0)) != cudaSuccess) return bail("mapped device pointer");
-  S->d_shared = reinterpret_cast<mvp::ServeShared *>(d);
-  S->d_ring = reinterpret_cast<mvp::ReqDesc *>(d + sizeof(mvp::ServeShared));
-  S->d_done = reinterpret_cast<mvp::ReqDone *>(d + sizeof(mvp::ServeShared) + sizeof(mvp::ReqDesc) * max_slots);
-  char *dev_state = nullptr;
-  size_t dev_bytes = 256 + sizeof(unsigned int) * max_slots + 256;
-  if ((e = cudaMalloc(&dev_state, dev_bytes)) != cudaSuccess) return bail("device state");
-  if ((e = cudaMemset(dev_state, 0, dev_bytes)) != cudaSuccess) return bail("device state reset");
-  S->d_claimed = reinterpret_cast<unsigned long long *>(dev_state);
-  S->d_status = reinterpret_cast<int *>(dev_state + 64);
-  S->d_tiles_done = reinterpret_cast<unsigned int *>(dev_state + 256);
-  if ((e = cudaStreamCreateWithFlags(&S->work, cudaStreamNonBlocking)) != cudaSuccess) return bail("work stream");
+  S->d_done = reinterpret_cast<mvp::ReqDone *>(d);
+  if ((e = cudaMalloc(&S->d_status, 256)) != cudaSuccess) return bail("status word");
+  if ((e = cudaMemset(S->d_status, 0, 256)) != cudaSuccess) return bail("status reset");
+  for (int i = 0; i < mvp::SERVE_STREAMS; ++i) {
+    Lane &L = S->lanes[i];
+    if ((e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking)) != cudaSuccess) return bail("stream");
+    if ((e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming)) != cudaSuccess) return bail("event");
+    if ((e = cudaHostAlloc(&L.h_reqs, sizeof(mvp::BatchReq) * max_slots, cudaHostAllocDefault)) != cudaSuccess)
+      return bail("batch staging");
+    if ((e = cudaMalloc(&L.d_reqs, sizeof(mvp::BatchReq) * max_slots)) != cudaSuccess) return bail("batch table");
+    if ((e = cudaMalloc(&L.d_counters, sizeof(unsigned int) * (max_slots + 1))) != cudaSuccess)
+      return bail("batch counters");
+  }
   if ((e = cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking)) != cudaSuccess) return bail("copy stream");
-  S->smem = sizeof(mvp::TileShared<mvp::SERVE_CAP>) * mvp::TILE_WARPS;
+  S->smem = (sizeof(mvp::TileShared<mvp::SERVE_CAP>) + sizeof(mvp::BatchReq)) * mvp::TILE_WARPS;
   if ((e = cudaFuncSetAttribute(mvp::k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem)) !=
       cudaSuccess)
     return bail("kernel attribute");
@@ -495,13 +462,20 @@ mvp_status mvp_serve_create(mvp_ctx *ctx, size_t hbm_budget, int32_t max_slots, 
 void mvp_serve_destroy(mvp_server *S) {
   if (!S) return;
   cudaSetDevice(S->device);
-  if (S->work) cudaStreamSynchronize(S->work);
+  for (auto &L : S->lanes)
+    if (L.stream) cudaStreamSynchronize(L.stream);
   if (S->copy) cudaStreamSynchronize(S->copy);
   for (auto &a : S->avatars) mvp::bvh_release(a.bvh);
   if (S->arena_base) cudaFree(S->arena_base);
-  if (S->d_claimed) cudaFree(S->d_claimed);
-  if (S->h_shared) cudaFreeHost(S->h_shared);
-  if (S->work) cudaStreamDestroy(S->work);
+  if (S->d_status) cudaFree(S->d_status);
+  if (S->h_done) cudaFreeHost(S->h_done);
+  for (auto &L : S->lanes) {
+    if (L.h_reqs) cudaFreeHost(L.h_reqs);
+    if (L.d_reqs) cudaFree(L.d_reqs);
+    if (L.d_counters) cudaFree(L.d_counters);
+    if (L.done) cudaEventDestroy(L.done);
+    if (L.stream) cudaStreamDestroy(L.stream);
+  }
   if (S->copy) cudaStreamDestroy(S->copy);
   delete S;
 }
@@ -541,8 +515,9 @@ mvp_status mvp_serve_submit(mvp_server *S, const mvp_request *req, uint64_t *tic
   std::lock_guard<std::mutex> lk(S->mu);
   if (req->avatar < 0 || req->avatar >= (int32_t)S->avatars.size())
     return serve_fail(MVP_ERR_INVALID_ARG, "unknown avatar");
-  if (req->width < 1 || req->height < 1 || !(req->focal > 0.0f) || !(req->dt > 0.0f) ||
-      !(req->t_far > req->t_near) || !(req->eps_early >= 0.0f && req->eps_early < 1.0f) ||
+  if (req->width < 1 || req->height < 1 || (int64_t)req->width * req->height > (int64_t)1 << 30 ||
+      !(req->focal > 0.0f) || !(req->dt > 0.0f) || !(req->t_far > req->t_near) ||
+      !(req->eps_early >= 0.0f && req->eps_early < 1.0f) ||
       mvp_num_steps(req->t_near, req->t_far, req->dt) > MVP_MAX_STEPS)
     return serve_fail(MVP_ERR_INVALID_ARG, "bad request parameters");
   for (int i = 0; i < 12; ++i)
@@ -574,7 +549,10 @@ mvp_status mvp_serve_poll(mvp_server *S, uint64_t ticket, float *out_rgba, doubl
     return serve_fail(MVP_ERR_INVALID_ARG, "unknown ticket");
   }
   InFlight f = it->second;
-  if (!is_done(S, f)) return MVP_NOT_READY;
+  if (!f.launched || !is_done(S, f)) {
+    mvp_status st = pump(S);
+    return st ? st : MVP_NOT_READY;
+  }
   const double ms = std::chrono::duration<double, std::milli>(clock_type::now() - f.submit).count();
   if (out_rgba) {
     cudaError_t e = cudaMemcpyAsync(out_rgba, S->arena_base + f.off, f.bytes, cudaMemcpyDefault, S->copy);
@@ -618,6 +596,7 @@ mvp_status mvp_serve_stats(mvp_server *S, mvp_serve_info *info) {
   cudaMemcpyAsync(&st, S->d_status, sizeof(int), cudaMemcpyDeviceToHost, S->copy);
   cudaStreamSynchronize(S->copy);
   info->device_status = st;
+  info->batches = (int64_t)S->batches;
   return MVP_OK;
 }
 
