@@ -86,47 +86,88 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
 #pragma unroll
       for (int c = 0; c < 12; ++c) acc[c] = 0.0f;
       const int e_lo = sh.elo[e], e_hi = sh.ehi[e];
+      const int64_t kbase = (int64_t)k * M2 * M;
+      int held = -1;  // voxel (within the primitive) whose cell corners are held
+      float4 c000, c001, c010, c011, c100, c101, c110, c111;
       for (int i = e_lo; i <= e_hi; ++i) {
-        if (i < lo || i > hi) continue;
-        const float ti = sample_t(a.t_near, a.dt, i);
-        const float x0 = fmaf(ti, L.d[0], L.o[0]);
-        const float x1 = fmaf(ti, L.d[1], L.o[1]);
-        const float x2 = fmaf(ti, L.d[2], L.o[2]);
-        float ux = fmaf(X.r0.x, x0, fmaf(X.r0.y, x1, fmaf(X.r0.z, x2, X.r0.w)));
-        float uy = fmaf(X.r1.x, x0, fmaf(X.r1.y, x1, fmaf(X.r1.z, x2, X.r1.w)));
-        float uz = fmaf(X.r2.x, x0, fmaf(X.r2.y, x1, fmaf(X.r2.z, x2, X.r2.w)));
-        const bool kx = ux >= 0.0f && ux <= Mm1, ky = uy >= 0.0f && uy <= Mm1, kz = uz >= 0.0f && uz <= Mm1;
-        ux = fminf(fmaxf(ux, 0.0f), Mm1);
-        uy = fminf(fmaxf(uy, 0.0f), Mm1);
-        uz = fminf(fmaxf(uz, 0.0f), Mm1);
-        const int ix = min((int)ux, M - 2), iy = min((int)uy, M - 2), iz = min((int)uz, M - 2);
-        const float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
-        const int vo = iz * M2 + iy * M + ix;  // voxel within the primitive
-        const int64_t v = (int64_t)k * M2 * M + vo;
-        const float4 c000 = Voxel<DT>::load(pbase, vo);
-        const float4 c001 = Voxel<DT>::load(pbase, vo + 1);
-        const float4 c010 = Voxel<DT>::load(pbase, vo + M);
-        const float4 c011 = Voxel<DT>::load(pbase, vo + M + 1);
-        const float4 c100 = Voxel<DT>::load(pbase, vo + M2);
-        const float4 c101 = Voxel<DT>::load(pbase, vo + M2 + 1);
-        const float4 c110 = Voxel<DT>::load(pbase, vo + M2 + M);
-        const float4 c111 = Voxel<DT>::load(pbase, vo + M2 + M + 1);
-        const float4 c00 = lerp4(c000, c001, fx), c01 = lerp4(c010, c011, fx);
-        const float4 c10 = lerp4(c100, c101, fx), c11 = lerp4(c110, c111, fx);
-        const float4 c0 = lerp4(c00, c01, fy), c1 = lerp4(c10, c11, fy);
-        const float4 val = lerp4(c0, c1, fz);
-        const bool at_clamp = i == i_clamp;
-        const float ga = at_clamp ? ga_s : ga_pre;
-        const float gr = at_clamp ? gsr : gcr, gg = at_clamp ? gsg : gcg, gb = at_clamp ? gsb : gcb;
-        // dL/d(rgba) of this primitive's sample
-        const float4 gv = make_float4(a.dt * val.w * gr, a.dt * val.w * gg, a.dt * val.w * gb,
-                                      a.dt * (ga + gr * val.x + gg * val.y + gb * val.z));
-        if (b.g_payload) {
-          float4 *G = reinterpret_cast<float4 *>(b.g_payload);
+        const bool in = i >= lo && i <= hi;
+        if (!in) continue;
+        float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+        float4 gv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        int vo = -1;
+        if (in) {
+          const float ti = sample_t(a.t_near, a.dt, i);
+          const float x0 = fmaf(ti, L.d[0], L.o[0]);
+          const float x1 = fmaf(ti, L.d[1], L.o[1]);
+          const float x2 = fmaf(ti, L.d[2], L.o[2]);
+          float ux = fmaf(X.r0.x, x0, fmaf(X.r0.y, x1, fmaf(X.r0.z, x2, X.r0.w)));
+          float uy = fmaf(X.r1.x, x0, fmaf(X.r1.y, x1, fmaf(X.r1.z, x2, X.r1.w)));
+          float uz = fmaf(X.r2.x, x0, fmaf(X.r2.y, x1, fmaf(X.r2.z, x2, X.r2.w)));
+          const bool kx = ux >= 0.0f && ux <= Mm1, ky = uy >= 0.0f && uy <= Mm1, kz = uz >= 0.0f && uz <= Mm1;
+          ux = fminf(fmaxf(ux, 0.0f), Mm1);
+          uy = fminf(fmaxf(uy, 0.0f), Mm1);
+          uz = fminf(fmaxf(uz, 0.0f), Mm1);
+          const int ix = min((int)ux, M - 2), iy = min((int)uy, M - 2), iz = min((int)uz, M - 2);
+          fx = ux - (float)ix;
+          fy = uy - (float)iy;
+          fz = uz - (float)iz;
+          vo = iz * M2 + iy * M + ix;  // voxel within the primitive
+          if (vo != held) {            // consecutive samples often stay in one cell
+            c000 = Voxel<DT>::load(pbase, vo);
+            c001 = Voxel<DT>::load(pbase, vo + 1);
+            c010 = Voxel<DT>::load(pbase, vo + M);
+            c011 = Voxel<DT>::load(pbase, vo + M + 1);
+            c100 = Voxel<DT>::load(pbase, vo + M2);
+            c101 = Voxel<DT>::load(pbase, vo + M2 + 1);
+            c110 = Voxel<DT>::load(pbase, vo + M2 + M);
+            c111 = Voxel<DT>::load(pbase, vo + M2 + M + 1);
+            held = vo;
+          }
+          const float4 c00 = lerp4(c000, c001, fx), c01 = lerp4(c010, c011, fx);
+          const float4 c10 = lerp4(c100, c101, fx), c11 = lerp4(c110, c111, fx);
+          const float4 c0 = lerp4(c00, c01, fy), c1 = lerp4(c10, c11, fy);
+          const float4 val = lerp4(c0, c1, fz);
+          const bool at_clamp = i == i_clamp;
+          const float ga = at_clamp ? ga_s : ga_pre;
+          const float gr = at_clamp ? gsr : gcr, gg = at_clamp ? gsg : gcg, gb = at_clamp ? gsb : gcb;
+          // dL/d(rgba) of this primitive's sample
+          gv = make_float4(a.dt * val.w * gr, a.dt * val.w * gg, a.dt * val.w * gb,
+                           a.dt * (ga + gr * val.x + gg * val.y + gb * val.z));
+          if (b.gmc) {
+            // dval/du along each axis (zero along an axis where u was clamped)
+            const float4 dx0 = lerp4(make_float4(c001.x - c000.x, c001.y - c000.y, c001.z - c000.z, c001.w - c000.w),
+                                     make_float4(c011.x - c010.x, c011.y - c010.y, c011.z - c010.z, c011.w - c010.w), fy);
+            const float4 dx1 = lerp4(make_float4(c101.x - c100.x, c101.y - c100.y, c101.z - c100.z, c101.w - c100.w),
+                                     make_float4(c111.x - c110.x, c111.y - c110.y, c111.z - c110.z, c111.w - c110.w), fy);
+            const float4 dvx = lerp4(dx0, dx1, fz);
+            const float4 dvy = lerp4(make_float4(c01.x - c00.x, c01.y - c00.y, c01.z - c00.z, c01.w - c00.w),
+                                     make_float4(c11.x - c10.x, c11.y - c10.y, c11.z - c10.z, c11.w - c10.w), fz);
+            const float4 dvz = make_float4(c1.x - c0.x, c1.y - c0.y, c1.z - c0.z, c1.w - c0.w);
+            const float gux = kx ? gv.x * dvx.x + gv.y * dvx.y + gv.z * dvx.z + gv.w * dvx.w : 0.0f;
+            const float guy = ky ? gv.x * dvy.x + gv.y * dvy.y + gv.z * dvy.z + gv.w * dvy.w : 0.0f;
+            const float guz = kz ? gv.x * dvz.x + gv.y * dvz.y + gv.z * dvz.z + gv.w * dvz.w : 0.0f;
+            const float p0 = x0 - tk.y, p1 = x1 - tk.z, p2 = x2 - tk.w;
+            acc[0] = fmaf(gux, p0, acc[0]);
+            acc[1] = fmaf(gux, p1, acc[1]);
+            acc[2] = fmaf(gux, p2, acc[2]);
+            acc[3] = fmaf(guy, p0, acc[3]);
+            acc[4] = fmaf(guy, p1, acc[4]);
+            acc[5] = fmaf(guy, p2, acc[5]);
+            acc[6] = fmaf(guz, p0, acc[6]);
+            acc[7] = fmaf(guz, p1, acc[7]);
+            acc[8] = fmaf(guz, p2, acc[8]);
+            acc[9] += gux;
+            acc[10] += guy;
+            acc[11] += guz;
+          }
+        }
+        if (in && b.g_payload) {
+          // the 8 corners of the cell get trilinear-weighted shares (float4 reductions)
+          float4 *G = reinterpret_cast<float4 *>(b.g_payload) + kbase + vo;
           const float wx0 = 1.0f - fx, wy0 = 1.0f - fy, wz0 = 1.0f - fz;
           const float w00 = wy0 * wz0, w01 = fy * wz0, w10 = wy0 * fz, w11 = fy * fz;
-#define MVP_SCATTER(off, WGT)                                                                    \
-  atomicAdd(G + v + (off), make_float4((WGT) * gv.x, (WGT) * gv.y, (WGT) * gv.z, (WGT) * gv.w))
+#define MVP_SCATTER(off, WGT) \
+  atomicAdd(G + (off), make_float4((WGT) * gv.x, (WGT) * gv.y, (WGT) * gv.z, (WGT) * gv.w))
           MVP_SCATTER(0, wx0 * w00);
           MVP_SCATTER(1, fx * w00);
           MVP_SCATTER(M, wx0 * w01);
@@ -136,33 +177,6 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
           MVP_SCATTER(M2 + M, wx0 * w11);
           MVP_SCATTER(M2 + M + 1, fx * w11);
 #undef MVP_SCATTER
-        }
-        if (b.gmc) {
-          // dval/du along each axis (zero along an axis where u was clamped)
-          const float4 dx0 = lerp4(make_float4(c001.x - c000.x, c001.y - c000.y, c001.z - c000.z, c001.w - c000.w),
-                                   make_float4(c011.x - c010.x, c011.y - c010.y, c011.z - c010.z, c011.w - c010.w), fy);
-          const float4 dx1 = lerp4(make_float4(c101.x - c100.x, c101.y - c100.y, c101.z - c100.z, c101.w - c100.w),
-                                   make_float4(c111.x - c110.x, c111.y - c110.y, c111.z - c110.z, c111.w - c110.w), fy);
-          const float4 dvx = lerp4(dx0, dx1, fz);
-          const float4 dvy = lerp4(make_float4(c01.x - c00.x, c01.y - c00.y, c01.z - c00.z, c01.w - c00.w),
-                                   make_float4(c11.x - c10.x, c11.y - c10.y, c11.z - c10.z, c11.w - c10.w), fz);
-          const float4 dvz = make_float4(c1.x - c0.x, c1.y - c0.y, c1.z - c0.z, c1.w - c0.w);
-          const float gux = kx ? gv.x * dvx.x + gv.y * dvx.y + gv.z * dvx.z + gv.w * dvx.w : 0.0f;
-          const float guy = ky ? gv.x * dvy.x + gv.y * dvy.y + gv.z * dvy.z + gv.w * dvy.w : 0.0f;
-          const float guz = kz ? gv.x * dvz.x + gv.y * dvz.y + gv.z * dvz.z + gv.w * dvz.w : 0.0f;
-          const float p0 = x0 - tk.y, p1 = x1 - tk.z, p2 = x2 - tk.w;
-          acc[0] = fmaf(gux, p0, acc[0]);
-          acc[1] = fmaf(gux, p1, acc[1]);
-          acc[2] = fmaf(gux, p2, acc[2]);
-          acc[3] = fmaf(guy, p0, acc[3]);
-          acc[4] = fmaf(guy, p1, acc[4]);
-          acc[5] = fmaf(guy, p2, acc[5]);
-          acc[6] = fmaf(guz, p0, acc[6]);
-          acc[7] = fmaf(guz, p1, acc[7]);
-          acc[8] = fmaf(guz, p2, acc[8]);
-          acc[9] += gux;
-          acc[10] += guy;
-          acc[11] += guz;
         }
       }
       if (b.gmc) {

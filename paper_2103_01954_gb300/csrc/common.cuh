@@ -114,9 +114,11 @@ __device__ __forceinline__ float sample_t(float t_near, float dt, int i) {
   return __fadd_rn(t_near, __fmul_rn((float)i, dt));
 }
 
-// Smallest i in [0, n] with t_i >= v (n if none). t_i is non-decreasing in i.
-__device__ __forceinline__ int first_sample_geq(float v, float t_near, float dt, int n) {
-  float x = (v - t_near) / dt;
+// Smallest i in [0, n] with t_i >= v (n if none). t_i is non-decreasing in i. The
+// estimate (v - t_near) * (1/dt) is only a starting point: the loops below make the
+// result exact against the sample times themselves.
+__device__ __forceinline__ int first_sample_geq(float v, float t_near, float dt, float inv_dt, int n) {
+  float x = (v - t_near) * inv_dt;
   int i;
   if (!(x > 0.0f)) i = 0;
   else if (x >= (float)n) i = n;
@@ -136,8 +138,8 @@ __device__ __forceinline__ int first_sample_geq(float v, float t_near, float dt,
 }
 
 // Smallest i in [0, n] with t_i > v (n if none).
-__device__ __forceinline__ int first_sample_gt(float v, float t_near, float dt, int n) {
-  float x = (v - t_near) / dt;
+__device__ __forceinline__ int first_sample_gt(float v, float t_near, float dt, float inv_dt, int n) {
+  float x = (v - t_near) * inv_dt;
   int i;
   if (x < 0.0f) i = 0;
   else if (x >= (float)n) i = n;

@@ -13,7 +13,13 @@
 
 #include "march.cuh"
 
+#ifndef MVP_MARCH_CHUNK
+#define MVP_MARCH_CHUNK 4
+#endif
+
 namespace mvp {
+
+constexpr int MARCH_CHUNK = MVP_MARCH_CHUNK;  // samples per chunk of the march loop
 
 // Voxel bytes per payload dtype.
 template <int DT>
@@ -76,82 +82,123 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
       wlen = (w1 - w0 + 1) >> 1;
       continue;
     }
+    // Samples go in chunks of MARCH_CHUNK: each window entry's transform is read from
+    // shared memory once per chunk, the chunk's samples give independent gathers, and
+    // a lane whose next sample stays in the same voxel cell of the same primitive
+    // reuses the 8 corners it already holds. Per sample, primitives are summed in
+    // entry order, as before; the composite then runs sample by sample.
     int i = w0;
     while (i < w1) {
       if (!__any_sync(FULL, alive)) break;
+      const int ie = min(i + MARCH_CHUNK, w1);
       uint32_t m0, m1;
-      int nxt = active_set<CAP>(sh, ne, i, w1, m0, m1);
+      const int nxt = active_chunk<CAP>(sh, ne, i, ie, w1, m0, m1);
       if ((m0 | m1) == 0) {
-        i = nxt;
+        i = max(nxt, ie);
         continue;
       }
-      for (; i < nxt; ++i) {
-        if (!__any_sync(FULL, alive)) break;
-        const float ti = sample_t(a.t_near, a.dt, i);
-        const float x0 = fmaf(ti, L.d[0], L.o[0]);
-        const float x1 = fmaf(ti, L.d[1], L.o[1]);
-        const float x2 = fmaf(ti, L.d[2], L.o[2]);
-        float sa = 0.0f, sr = 0.0f, sg = 0.0f, sb = 0.0f;
-        uint32_t b0 = m0, b1 = m1;
-        while (b0 | b1) {
-          int e;
-          if (b0) { e = __ffs(b0) - 1; b0 &= b0 - 1; }
-          else { e = 32 + __ffs(b1) - 1; b1 &= b1 - 1; }
-          const uint32_t rg = sh.erng[e][lane];
-          const bool in = alive && i >= (int)(rg & 0xffffu) && i <= (int)(rg >> 16);
-          if (in) {
-            const Xform X = sh.exf[e];
-            // voxel coordinate u = Mx x + c (FP32, the cell decision of the oracle's
-            // FP32 mode), clamped into the box
-            float ux = fmaf(X.r0.x, x0, fmaf(X.r0.y, x1, fmaf(X.r0.z, x2, X.r0.w)));
-            float uy = fmaf(X.r1.x, x0, fmaf(X.r1.y, x1, fmaf(X.r1.z, x2, X.r1.w)));
-            float uz = fmaf(X.r2.x, x0, fmaf(X.r2.y, x1, fmaf(X.r2.z, x2, X.r2.w)));
-            ux = fminf(fmaxf(ux, 0.0f), Mm1);
-            uy = fminf(fmaxf(uy, 0.0f), Mm1);
-            uz = fminf(fmaxf(uz, 0.0f), Mm1);
-            const int ix = min((int)ux, M - 2), iy = min((int)uy, M - 2), iz = min((int)uz, M - 2);
-            const float4 val = trilinear<DT, MT>(sh.eptr[e], M, ix, iy, iz, ux - (float)ix, uy - (float)iy,
-                                                 uz - (float)iz);
-            sa += val.w;
-            sr = fmaf(val.w, val.x, sr);
-            sg = fmaf(val.w, val.y, sg);
-            sb = fmaf(val.w, val.z, sb);
-            if (COUNT) ++n_eval;
+      float xs[MARCH_CHUNK][3];
+#pragma unroll
+      for (int c = 0; c < MARCH_CHUNK; ++c) {
+        const float ti = sample_t(a.t_near, a.dt, i + c);
+        xs[c][0] = fmaf(ti, L.d[0], L.o[0]);
+        xs[c][1] = fmaf(ti, L.d[1], L.o[1]);
+        xs[c][2] = fmaf(ti, L.d[2], L.o[2]);
+      }
+      float sa[MARCH_CHUNK], sr[MARCH_CHUNK], sg[MARCH_CHUNK], sb[MARCH_CHUNK];
+      int ne_c[MARCH_CHUNK];  // evaluations per sample (count variant)
+#pragma unroll
+      for (int c = 0; c < MARCH_CHUNK; ++c) {
+        sa[c] = sr[c] = sg[c] = sb[c] = 0.0f;
+        ne_c[c] = 0;
+      }
+      uint32_t b0 = m0, b1 = m1;
+      while (b0 | b1) {
+        int e;
+        if (b0) { e = __ffs(b0) - 1; b0 &= b0 - 1; }
+        else { e = 32 + __ffs(b1) - 1; b1 &= b1 - 1; }
+        const uint32_t rg = sh.erng[e][lane];
+        const int lo = max((int)(rg & 0xffffu), i), hi = min((int)(rg >> 16), ie - 1);
+        if (!alive || lo > hi) continue;
+        const Xform X = sh.exf[e];
+        const char *pbase = sh.eptr[e];
+        int held = -1;  // voxel (within the primitive) of the corners held
+        float4 c000, c001, c010, c011, c100, c101, c110, c111;
+#pragma unroll
+        for (int c = 0; c < MARCH_CHUNK; ++c) {
+          const int ii = i + c;
+          if (ii < lo || ii > hi) continue;
+          // voxel coordinate u = Mx x + c (FP32, the cell decision of the oracle's
+          // FP32 mode), clamped into the box
+          float ux = fmaf(X.r0.x, xs[c][0], fmaf(X.r0.y, xs[c][1], fmaf(X.r0.z, xs[c][2], X.r0.w)));
+          float uy = fmaf(X.r1.x, xs[c][0], fmaf(X.r1.y, xs[c][1], fmaf(X.r1.z, xs[c][2], X.r1.w)));
+          float uz = fmaf(X.r2.x, xs[c][0], fmaf(X.r2.y, xs[c][1], fmaf(X.r2.z, xs[c][2], X.r2.w)));
+          ux = fminf(fmaxf(ux, 0.0f), Mm1);
+          uy = fminf(fmaxf(uy, 0.0f), Mm1);
+          uz = fminf(fmaxf(uz, 0.0f), Mm1);
+          const int ix = min((int)ux, M - 2), iy = min((int)uy, M - 2), iz = min((int)uz, M - 2);
+          const int v = (iz * M + iy) * M + ix;
+          if (v != held) {
+            const void *p = pbase;
+            c000 = Voxel<DT>::load(p, v);
+            c001 = Voxel<DT>::load(p, v + 1);
+            c010 = Voxel<DT>::load(p, v + M);
+            c011 = Voxel<DT>::load(p, v + M + 1);
+            c100 = Voxel<DT>::load(p, v + M * M);
+            c101 = Voxel<DT>::load(p, v + M * M + 1);
+            c110 = Voxel<DT>::load(p, v + M * M + M);
+            c111 = Voxel<DT>::load(p, v + M * M + M + 1);
+            held = v;
           }
+          const float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
+          const float4 c00 = lerp4(c000, c001, fx), c01 = lerp4(c010, c011, fx);
+          const float4 c10 = lerp4(c100, c101, fx), c11 = lerp4(c110, c111, fx);
+          const float4 q0 = lerp4(c00, c01, fy), q1 = lerp4(c10, c11, fy);
+          const float4 val = lerp4(q0, q1, fz);
+          sa[c] += val.w;
+          sr[c] = fmaf(val.w, val.x, sr[c]);
+          sg[c] = fmaf(val.w, val.y, sg[c]);
+          sb[c] = fmaf(val.w, val.z, sb[c]);
+          if (COUNT) ++ne_c[c];
         }
-        if (alive) {
-          // clamped additive accumulation: w = min(a, 1 - T), I += c w / a, T += w
-          const float aa = sa * a.dt;
-          const float cr = sr * a.dt, cg = sg * a.dt, cb = sb * a.dt;
-          const float rem = 1.0f - T;
-          if (aa <= rem) {
-            Ir += cr;
-            Ig += cg;
-            Ib += cb;
-            T = fminf(T + aa, 1.0f);
-            if (T >= a.stop_T) {
-              alive = false;
-              if (!COUNT && a.saved) {
-                Saved S = {0.0f, 0.0f, 0.0f, 0.0f, i, -1};
-                a.saved[L.r] = S;
-              }
-              saved_done = true;
-            }
-          } else {
-            const float bt = rem / aa;
-            Ir = fmaf(cr, bt, Ir);
-            Ig = fmaf(cg, bt, Ig);
-            Ib = fmaf(cb, bt, Ib);
-            T = 1.0f;
-            alive = false;  // T = 1 >= 1 - eps_early
+      }
+#pragma unroll
+      for (int c = 0; c < MARCH_CHUNK; ++c) {
+        const int ii = i + c;
+        if (!alive || ii >= ie) continue;
+        if (COUNT) n_eval += ne_c[c];  // samples past a ray's termination are not counted
+        // clamped additive accumulation: w = min(a, 1 - T), I += c w / a, T += w
+        const float aa = sa[c] * a.dt;
+        const float cr = sr[c] * a.dt, cg = sg[c] * a.dt, cb = sb[c] * a.dt;
+        const float rem = 1.0f - T;
+        if (aa <= rem) {
+          Ir += cr;
+          Ig += cg;
+          Ib += cb;
+          T = fminf(T + aa, 1.0f);
+          if (T >= a.stop_T) {
+            alive = false;
             if (!COUNT && a.saved) {
-              Saved S = {cr / aa, cg / aa, cb / aa, bt, i, i};
+              Saved S = {0.0f, 0.0f, 0.0f, 0.0f, ii, -1};
               a.saved[L.r] = S;
             }
             saved_done = true;
           }
+        } else {
+          const float bt = rem / aa;
+          Ir = fmaf(cr, bt, Ir);
+          Ig = fmaf(cg, bt, Ig);
+          Ib = fmaf(cb, bt, Ib);
+          T = 1.0f;
+          alive = false;  // T = 1 >= 1 - eps_early
+          if (!COUNT && a.saved) {
+            Saved S = {cr / aa, cg / aa, cb / aa, bt, ii, ii};
+            a.saved[L.r] = S;
+          }
+          saved_done = true;
         }
       }
+      i = ie;
     }
     w0 = w1;
     wlen = min(a.n_steps, wlen * 2);

@@ -235,21 +235,31 @@ __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__r
   int ne = 0;
   bool live = L.r >= 0 && lane_last >= w0;
   int hi_cap = min(w1 - 1, lane_last);
+  const float inv_dt = 1.0f / dt;
   auto emit = [&](int nc) -> bool {
     for (int c = 0; c < nc; ++c) {
-      int k = sh.cand[c];
-      const float4 *pp = reinterpret_cast<const float4 *>(pose + k);
+      if ((c & 31) == 0 && c + lane < nc) {
+        // pull the next 32 candidates' poses (one 64-byte line each) into L1 at once,
+        // so the loads below do not wait on L2 one candidate after another
+        const Pose *pp = pose + sh.cand[c + lane];
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(pp));
+      }
+      const int k = sh.cand[c];
+      float4 pk[4];
+      const float4 *qa = reinterpret_cast<const float4 *>(pose + k);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) pk[j] = __ldg(qa + j);
       Pose Pk;
-      Pk.p0 = __ldg(pp);
-      Pk.p1 = __ldg(pp + 1);
-      Pk.p2 = __ldg(pp + 2);
-      Pk.p3 = __ldg(pp + 3);
+      Pk.p0 = pk[0];
+      Pk.p1 = pk[1];
+      Pk.p2 = pk[2];
+      Pk.p3 = pk[3];
       int ilo = 1, ihi = 0;
       if (live) {
         float tin, tout;
         if (slab_spec(Pk, L.o[0], L.o[1], L.o[2], L.d[0], L.d[1], L.d[2], t_near, t_far, tin, tout)) {
-          ilo = max(first_sample_geq(tin, t_near, dt, n_steps), w0);
-          ihi = min(first_sample_gt(tout, t_near, dt, n_steps) - 1, hi_cap);
+          ilo = max(first_sample_geq(tin, t_near, dt, inv_dt, n_steps), w0);
+          ihi = min(first_sample_gt(tout, t_near, dt, inv_dt, n_steps) - 1, hi_cap);
         }
       }
       bool has = ilo <= ihi;
@@ -262,11 +272,6 @@ __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__r
         sh.ek[ne] = k;
         sh.elo[ne] = lo_min;
         sh.ehi[ne] = hi_max;
-        const float4 *xp = reinterpret_cast<const float4 *>(xf + k);
-        sh.exf[ne].r0 = __ldg(xp);
-        sh.exf[ne].r1 = __ldg(xp + 1);
-        sh.exf[ne].r2 = __ldg(xp + 2);
-        sh.eptr[ne] = payload + (int64_t)k * prim_bytes;
       }
       ++ne;
     }
@@ -276,7 +281,18 @@ __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__r
   float slack = 1.0e-5f * (fabsf(ta) + fabsf(tb)) + 1.0e-30f;
   bool ok = traverse_tile(sh, nodes, n_prims, ta - slack, tb + slack, emit);
   __syncwarp();
-  return ok ? ne : -1;
+  if (!ok) return -1;
+  // the entries' march transforms and payload pointers, loaded in parallel
+  for (int e = lane; e < ne; e += 32) {
+    const int k = sh.ek[e];
+    const float4 *xp = reinterpret_cast<const float4 *>(xf + k);
+    sh.exf[e].r0 = __ldg(xp);
+    sh.exf[e].r1 = __ldg(xp + 1);
+    sh.exf[e].r2 = __ldg(xp + 2);
+    sh.eptr[e] = payload + (int64_t)k * prim_bytes;
+  }
+  __syncwarp();
+  return ne;
 }
 
 // Active entries at sample i (two 32-bit masks) and the next sample at which the
@@ -297,6 +313,31 @@ __device__ __forceinline__ int active_set(const TileShared<CAP> &sh, int ne, int
     a1 = lo <= i && i <= hi;
     int v = lo > i ? lo : (hi >= i ? hi + 1 : 0x7fffffff);
     nxt = min(nxt, v);
+  }
+  m0 = __ballot_sync(FULL, a0);
+  m1 = __ballot_sync(FULL, a1);
+  nxt = __reduce_min_sync(FULL, nxt);
+  return min(nxt, w1);
+}
+
+// Entries whose tile sample range meets the chunk [i, ie) (two 32-bit masks), and
+// the first sample at or after ie where some entry starts (w1 if none): where the
+// chunk is empty the march jumps there.
+template <int CAP>
+__device__ __forceinline__ int active_chunk(const TileShared<CAP> &sh, int ne, int i, int ie, int w1, uint32_t &m0,
+                                            uint32_t &m1) {
+  const int lane = threadIdx.x & 31;
+  int nxt = 0x7fffffff;
+  bool a0 = false, a1 = false;
+  if (lane < ne) {
+    const int lo = sh.elo[lane], hi = sh.ehi[lane];
+    a0 = lo < ie && hi >= i;
+    if (lo >= ie) nxt = lo;
+  }
+  if (CAP > 32 && lane + 32 < ne) {
+    const int lo = sh.elo[lane + 32], hi = sh.ehi[lane + 32];
+    a1 = lo < ie && hi >= i;
+    if (lo >= ie) nxt = min(nxt, lo);
   }
   m0 = __ballot_sync(FULL, a0);
   m1 = __ballot_sync(FULL, a1);
