@@ -197,14 +197,14 @@ MVP_API mvp_status mvp_camera_rays(mvp_ctx *ctx, const float *c2w, float focal, 
 
 /* ------------------------------------------------------------ serving */
 /* Continuous batching of render requests (avatar = resident primitive set,
- * camera, resolution). Admitted requests are launched as a batch: one persistent
- * grid whose warps claim the batch's 8x4-pixel tiles, generate their pinhole rays
- * and march them with the code of mvp_raymarch_fwd, so a request's image equals
- * mvp_camera_rays + mvp_raymarch_fwd on the same avatar, alone or in any mix.
- * Requests arriving while batches run form the next batch on another of 4 streams,
- * whose blocks start as SMs free up, so requests overlap on the device; each
- * request completes as soon as its own tiles are done. No device code waits for
- * anything. Admission: a request needs a free slot, and its image
+ * camera, resolution). Each admitted request is launched at once, on the least
+ * loaded of 8 streams, as a grid with one warp per 8x4-pixel tile that generates
+ * its pinhole rays and marches them with the code of mvp_raymarch_fwd, so a
+ * request's image equals mvp_camera_rays + mvp_raymarch_fwd on the same avatar,
+ * alone or in any mix. Requests in flight overlap on the device (a request's
+ * blocks start as SMs free up from the ones before it); each completes as soon as
+ * its own tiles are done, seen by the host through mapped memory. No device code
+ * waits for anything. Admission: a request needs a free slot, and its image
  * (width*height*16 bytes) must fit the HBM budget (resident avatars + images in
  * flight) and the server's image arena; otherwise it queues (FIFO) and is admitted
  * by a later submit or poll. All calls are thread-safe. */
@@ -222,10 +222,11 @@ typedef struct mvp_request {
 typedef struct mvp_serve_info {
   int64_t pending, in_flight, max_in_flight, completed;
   int64_t resident_bytes, in_flight_bytes;
-  int32_t grid_blocks, avatars;
+  int32_t grid_blocks;    /* blocks of the serving kernel resident on the GPU at once */
+  int32_t avatars;
   int32_t device_status;  /* status bits set by the serving kernel (0: none) */
   int32_t reserved;
-  int64_t batches;        /* batch launches so far */
+  int64_t batches;        /* request launches so far */
 } mvp_serve_info;
 
 /* hbm_budget: bytes for resident avatars (payload + BVH) plus images in flight;

@@ -4,10 +4,6 @@
 
 namespace mvp {
 
-#ifndef MVP_MARCH_MINB
-#define MVP_MARCH_MINB 5
-#endif
-
 template <int DT, int CAP, bool COUNT, int MT>
 __global__ void __launch_bounds__(TILE_WARPS * 32, MVP_MARCH_MINB) k_march(MarchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -10,6 +10,10 @@ namespace mvp {
 #endif
 constexpr int MARCH_CAP = MVP_MARCH_CAP;  // primitives a warp tile holds per depth window
 
+#ifndef MVP_MARCH_MINB
+#define MVP_MARCH_MINB 5  // resident blocks per SM the march kernels are compiled for
+#endif
+
 struct MarchArgs {
   // primitives and their BVH
   int n_prims, M, dtype;

@@ -1,24 +1,21 @@
 // serve.cu -- continuous batching of render requests (different avatars, cameras
-// and resolutions), each batch in one persistent kernel launch.
+// and resolutions) on one GPU.
 //
-// Device side. A batch is a list of admitted requests; each request is cut into
-// warp tiles of 8x4 pixels numbered consecutively across the batch. The batch's
-// grid (one CTA set per SM) has every warp claim tile numbers from the batch's own
-// counter, find the owning request (its descriptor is copied once into shared
-// memory), generate the tile's pinhole rays and march it with the same code as
-// mvp_raymarch_fwd (march_tile). A warp past the batch's last tile returns: nothing
-// on the device ever waits. The warp that finishes a request's last tile publishes
-// its completion to mapped host memory (system-scope release), so a small request
-// completes without waiting for the rest of its batch.
+// Device side. Each admitted request is one launch of k_serve, its arguments in the
+// kernel's parameter block, with one warp per 8x4-pixel tile of its image. A warp
+// generates its tile's pinhole rays and marches them with the same code as
+// mvp_raymarch_fwd (march_tile, specialised for M = 8, 16, 32 and for the payload
+// type). Nothing on the device ever waits. The warp that counts a request's last
+// tile publishes its completion to mapped host memory (system-scope release), so the
+// host sees it without synchronising a stream.
 //
 // Host side. Admission: a request needs a free slot and its image (W*H*16 bytes)
 // must fit the HBM budget (resident avatars + images in flight) and the server's
 // image arena; otherwise it waits in a FIFO and is admitted by a later submit or
-// poll as slots and memory free up. Admitted requests are launched as a batch on
-// one of several streams as soon as one is idle; requests that arrive while batches
-// run form the next batch on another stream, whose blocks start as SMs free up, so
-// requests overlap on the device. A request larger than the budget is refused
-// (MVP_ERR_CAPACITY).
+// poll as slots and memory free up. An admitted request is launched at once on the
+// least loaded of several streams, so requests overlap on the device: a new
+// request's blocks start as SMs free up from the ones before it. A request larger
+// than the budget is refused (MVP_ERR_CAPACITY).
 #include <math.h>
 #include <string.h>
 
@@ -35,31 +32,25 @@
 namespace mvp {
 
 constexpr int SERVE_CAP = MARCH_CAP;
-constexpr int SERVE_STREAMS = 4;  // batches that may run at once
-
-// One request of a batch (device memory, copied in before the batch's launch).
-struct BatchReq {
-  unsigned long long seq;  // request sequence number
-  int slot;                // completion record index
-  int tile_begin;          // first tile of the request within the batch
-  int n_tiles;
-  int n_prims, M, dtype, n_steps, width, height;
-  const void *payload;
-  const Node *nodes;
-  const Pose *pose;
-  const Xform *xf;
-  float *out;
-  float c2w[12];
-  float focal, t_near, t_far, dt, stop_T;
-  float bg[3];
-  int pad;
-};
+constexpr int SERVE_STREAMS = 8;  // requests that may run at once without queueing on a stream
 
 // Completion record of a slot (mapped host memory): written by the device.
 struct ReqDone {
   unsigned long long seq_done;  // 1 + sequence number of the request completed in this slot (0: none)
   unsigned long long t_start_ns, t_end_ns;
   unsigned long long pad;
+};
+
+// One request: the kernel's parameter block (constant bank), so the march reads its
+// arguments exactly as mvp_raymarch_fwd's kernel does.
+struct ServeReq {
+  MarchArgs m;               // payload, BVH, sampling, output image (m.o, m.d unused)
+  float c2w[12];
+  float focal;
+  int slot;                  // completion record and tile counter index
+  unsigned long long seq;    // request sequence number
+  unsigned int *tiles_done;  // device, per slot; zero between requests
+  ReqDone *done;             // mapped host memory, per slot
 };
 
 __device__ __forceinline__ void st_release_sys(unsigned long long *p, unsigned long long v) {
@@ -72,108 +63,55 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   return t;
 }
 
-struct BatchArgs {
-  const BatchReq *reqs;     // device, n_req entries
-  int n_req;
-  int total_tiles;
-  unsigned int *claimed;    // device, zeroed before the launch
-  unsigned int *tiles_done; // device, n_req entries, zeroed before the launch
-  ReqDone *done;            // mapped host memory, indexed by slot
-  int *status;
-};
-
-template <int DT>
-__device__ __noinline__ void serve_tile(TileShared<SERVE_CAP> &sh, const MarchArgs &a, const LaneRay &L) {
-  march_tile<DT, SERVE_CAP, false, 0>(sh, a, L);
-}
-
-__global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_serve(BatchArgs A) {
+// One warp per warp tile of the request's image, specialised by payload type and
+// resolution class (MT = M for M = 8, 16, 32, else 0: any M). The warp that counts
+// the last tile publishes the completion and resets the slot's counter for its next
+// request (every other warp of this request has counted by then).
+template <int DT, int MT>
+__global__ void __launch_bounds__(TILE_WARPS * 32, MVP_MARCH_MINB) k_serve(const __grid_constant__ ServeReq R) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   TileShared<SERVE_CAP> &sh = reinterpret_cast<TileShared<SERVE_CAP> *>(smem_raw)[warp];
-  BatchReq &D = reinterpret_cast<BatchReq *>(smem_raw + sizeof(TileShared<SERVE_CAP>) * TILE_WARPS)[warp];
-  int cur = -1, c_begin = 0, c_n = 0;
-  while (true) {
-    unsigned int tl = 0;
-    if (lane == 0) tl = atomicAdd(A.claimed, 1u);
-    const int t = (int)__shfl_sync(FULL, tl, 0);
-    if (t >= A.total_tiles) return;
-    if (cur < 0 || t < c_begin || t >= c_begin + c_n) {
-      // owning request: the last one whose first tile is <= t (requests are in tile order)
-      int lo = 0, hi = A.n_req - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(&A.reqs[mid].tile_begin) <= t) lo = mid; else hi = mid - 1;
-      }
-      cur = lo;
-      constexpr int W = (int)(sizeof(BatchReq) / 4);
-      static_assert(sizeof(BatchReq) % 4 == 0 && W <= 64, "descriptor copy");
-      const unsigned int *src = reinterpret_cast<const unsigned int *>(&A.reqs[cur]);
-      unsigned int *dst = reinterpret_cast<unsigned int *>(&D);
-      __syncwarp();
-      for (int w = lane; w < W; w += 32) dst[w] = __ldg(src + w);
-      __syncwarp();
-      c_begin = D.tile_begin;
-      c_n = D.n_tiles;
-    }
-    if (lane == 0 && t == c_begin) A.done[D.slot].t_start_ns = globaltimer();
-    MarchArgs a;
-    a.n_prims = D.n_prims;
-    a.M = D.M;
-    a.dtype = D.dtype;
-    a.payload = D.payload;
-    a.nodes = D.nodes;
-    a.pose = D.pose;
-    a.xf = D.xf;
-    const int width = D.width, height = D.height;
-    a.geom.n_rays = (int64_t)width * height;
-    a.geom.width = width;
-    a.geom.height = height;
-    a.geom.n_warp_tiles = D.n_tiles;
-    a.o = a.d = nullptr;
-    a.t_near = D.t_near;
-    a.t_far = D.t_far;
-    a.dt = D.dt;
-    a.stop_T = D.stop_T;
-    a.bg[0] = D.bg[0];
-    a.bg[1] = D.bg[1];
-    a.bg[2] = D.bg[2];
-    a.n_steps = D.n_steps;
-    a.out = D.out;
-    a.saved = nullptr;
-    a.n_eval = nullptr;
-    a.status = A.status;
-    LaneRay L;
-    const int64_t r = tile_ray(a.geom, (int64_t)(t - c_begin), lane);
-    L.r = r;
-    if (r >= 0) {
-      const int row = (int)(r / width), col = (int)(r - (int64_t)row * width);
-      camera_ray(D.c2w, D.focal, width, height, row, col, L.o, L.d);
-    } else {
+  const int64_t wt = (int64_t)blockIdx.x * TILE_WARPS + warp;
+  const int64_t n_tiles = R.m.geom.n_warp_tiles;
+  if (wt >= n_tiles) return;
+  if (lane == 0 && wt == 0) R.done[R.slot].t_start_ns = globaltimer();
+  LaneRay L;
+  const int64_t r = tile_ray(R.m.geom, wt, lane);
+  L.r = r;
+  if (r >= 0) {
+    const int width = R.m.geom.width;
+    const int row = (int)(r / width), col = (int)(r - (int64_t)row * width);
+    camera_ray(R.c2w, R.focal, width, R.m.geom.height, row, col, L.o, L.d);
+  } else {
 #pragma unroll
-      for (int j = 0; j < 3; ++j) L.o[j] = L.d[j] = 0.0f;
+    for (int j = 0; j < 3; ++j) L.o[j] = L.d[j] = 0.0f;
+  }
+  if (__ballot_sync(FULL, r >= 0) != 0) march_tile<DT, SERVE_CAP, false, MT>(sh, R.m, L);
+  __syncwarp();
+  if (lane == 0) {
+    __threadfence();  // this tile's pixels are visible before it is counted
+    unsigned int *cnt = R.tiles_done + R.slot;
+    const unsigned int fin = atomicAdd(cnt, 1u);
+    if (fin + 1 == (unsigned int)n_tiles) {
+      *cnt = 0u;
+      __threadfence();
+      R.done[R.slot].t_end_ns = globaltimer();
+      __threadfence_system();
+      st_release_sys(&R.done[R.slot].seq_done, R.seq + 1);
     }
-    if (__ballot_sync(FULL, r >= 0) != 0) {
-      switch (a.dtype) {
-        case MVP_F32: serve_tile<MVP_F32>(sh, a, L); break;
-        case MVP_BF16: serve_tile<MVP_BF16>(sh, a, L); break;
-        default: serve_tile<MVP_F16>(sh, a, L); break;
-      }
-    }
-    __syncwarp();
-    if (lane == 0) {
-      __threadfence();  // this tile's pixels are visible before it is counted
-      const unsigned int fin = atomicAdd(&A.tiles_done[cur], 1u);
-      if (fin + 1 == (unsigned int)c_n) {
-        __threadfence();
-        A.done[D.slot].t_end_ns = globaltimer();
-        __threadfence_system();
-        st_release_sys(&A.done[D.slot].seq_done, D.seq + 1);
-      }
-    }
-    __syncwarp();
   }
 }
+
+// Kernel of a payload: dtype x {M = 8, 16, 32, other}.
+inline int serve_class(int dtype, int M) { return dtype * 4 + (M == 8 ? 0 : M == 16 ? 1 : M == 32 ? 2 : 3); }
+constexpr int SERVE_CLASSES = 12;
+
+using ServeKernel = void (*)(const ServeReq);
+static const ServeKernel k_serve_table[SERVE_CLASSES] = {
+    k_serve<MVP_F32, 8>,  k_serve<MVP_F32, 16>,  k_serve<MVP_F32, 32>,  k_serve<MVP_F32, 0>,
+    k_serve<MVP_BF16, 8>, k_serve<MVP_BF16, 16>, k_serve<MVP_BF16, 32>, k_serve<MVP_BF16, 0>,
+    k_serve<MVP_F16, 8>,  k_serve<MVP_F16, 16>,  k_serve<MVP_F16, 32>,  k_serve<MVP_F16, 0>};
 
 }  // namespace mvp
 
@@ -197,10 +135,10 @@ struct Pending {
 struct InFlight {
   uint64_t seq = 0;
   int slot = -1;
+  int stream = -1;  // index into mvp_server::streams
   size_t off = 0, bytes = 0;
   mvp_request req;
   clock_type::time_point submit;
-  bool launched = false;
 };
 
 // First-fit allocator over the image arena (host bookkeeping only).
@@ -243,18 +181,6 @@ struct Arena {
   }
 };
 
-// Per-stream batch buffers: the batch table is staged in pinned memory and copied to
-// the device on the stream before the launch; the stream is reused only after its
-// previous batch (and that copy) finished.
-struct Lane {
-  cudaStream_t stream = nullptr;
-  cudaEvent_t done = nullptr;
-  bool busy = false;
-  mvp::BatchReq *h_reqs = nullptr;  // pinned staging
-  mvp::BatchReq *d_reqs = nullptr;
-  unsigned int *d_counters = nullptr;  // [0] claimed, [1..] tiles done per request
-};
-
 }  // namespace
 
 struct mvp_server {
@@ -269,7 +195,10 @@ struct mvp_server {
   char *arena_base = nullptr;
   mvp::ReqDone *h_done = nullptr, *d_done = nullptr;  // mapped
   int *d_status = nullptr;
-  Lane lanes[mvp::SERVE_STREAMS];
+  unsigned int *d_tiles_done = nullptr;  // per slot
+  cudaStream_t streams[mvp::SERVE_STREAMS] = {};
+  int outstanding[mvp::SERVE_STREAMS] = {};  // requests launched and not yet collected
+  int next_stream = 0;
   cudaStream_t copy = nullptr;
   int grid = 0;
   size_t smem = 0;
@@ -278,7 +207,7 @@ struct mvp_server {
   std::deque<Pending> pending;
   std::map<uint64_t, InFlight> inflight;  // ticket -> request (admitted)
   size_t max_inflight_seen = 0;
-  uint64_t completed = 0, batches = 0;
+  uint64_t completed = 0, launches = 0;
 };
 
 namespace {
@@ -290,11 +219,55 @@ mvp_status serve_fail(mvp_status s, const char *msg) {
 
 size_t image_bytes(const mvp_request &r) { return (size_t)r.width * (size_t)r.height * 4 * sizeof(float); }
 
-int warp_tiles(int w, int h) { return ((w + 15) / 16) * ((h + 7) / 8) * 4; }
+// Launch one admitted request on the stream with the fewest requests outstanding
+// (round robin among ties): its image's warp tiles run as soon as SMs free up,
+// beside the requests on the other streams.
+mvp_status launch(mvp_server *S, InFlight &f) {
+  const mvp_request &q = f.req;
+  const Avatar &A = S->avatars[q.avatar];
+  mvp::ServeReq R;
+  memset(&R, 0, sizeof(R));
+  mvp::MarchArgs &m = R.m;
+  m.n_prims = A.prims.n;
+  m.M = A.prims.M;
+  m.dtype = A.prims.dtype;
+  m.payload = A.prims.payload;
+  m.nodes = A.bvh.nodes;
+  m.pose = A.bvh.pose;
+  m.xf = A.bvh.xf;
+  m.geom = mvp::make_tile_geom((int64_t)q.width * q.height, q.width, q.height);
+  m.t_near = q.t_near;
+  m.t_far = q.t_far;
+  m.dt = q.dt;
+  m.stop_T = (float)(1.0 - (double)q.eps_early);
+  memcpy(m.bg, q.bg, sizeof(m.bg));
+  m.n_steps = (int)mvp_num_steps(q.t_near, q.t_far, q.dt);
+  m.out = reinterpret_cast<float *>(S->arena_base + f.off);
+  m.status = S->d_status;
+  memcpy(R.c2w, q.c2w, sizeof(R.c2w));
+  R.focal = q.focal;
+  R.slot = f.slot;
+  R.seq = f.seq;
+  R.tiles_done = S->d_tiles_done;
+  R.done = S->d_done;
+  int best = -1;
+  for (int k = 0; k < mvp::SERVE_STREAMS; ++k) {
+    const int i = (S->next_stream + k) % mvp::SERVE_STREAMS;
+    if (best < 0 || S->outstanding[i] < S->outstanding[best]) best = i;
+  }
+  S->next_stream = (best + 1) % mvp::SERVE_STREAMS;
+  const unsigned blocks = (unsigned)(m.geom.n_warp_tiles / mvp::TILE_WARPS);
+  mvp::k_serve_table[mvp::serve_class(m.dtype, m.M)]<<<blocks, mvp::TILE_WARPS * 32, S->smem, S->streams[best]>>>(R);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return serve_fail(MVP_ERR_CUDA, cudaGetErrorString(e));
+  f.stream = best;
+  S->outstanding[best]++;
+  S->launches++;
+  return MVP_OK;
+}
 
 // Admit pending requests in FIFO order while a slot, budget and arena space allow,
-// then launch the admitted, not yet launched requests as one batch on an idle
-// stream. Called with S->mu held.
+// launching each as it is admitted. Called with S->mu held.
 mvp_status pump(mvp_server *S) {
   while (!S->pending.empty()) {
     Pending &p = S->pending.front();
@@ -317,81 +290,17 @@ mvp_status pump(mvp_server *S) {
     f.req = p.req;
     f.submit = p.submit;
     __atomic_store_n(&S->h_done[slot].seq_done, 0ull, __ATOMIC_RELEASE);
+    const mvp_status st = launch(S, f);
+    if (st != MVP_OK) {
+      S->arena.release(off, bytes);
+      return st;
+    }
     S->slot_busy[slot] = true;
     S->inflight[p.ticket] = f;
     S->inflight_bytes += bytes;
     if (S->inflight.size() > S->max_inflight_seen) S->max_inflight_seen = S->inflight.size();
     S->pending.pop_front();
   }
-  // anything admitted but not launched?
-  bool any = false;
-  for (auto &kv : S->inflight)
-    if (!kv.second.launched) {
-      any = true;
-      break;
-    }
-  if (!any) return MVP_OK;
-  // an idle stream (its previous batch finished)
-  Lane *L = nullptr;
-  for (int i = 0; i < mvp::SERVE_STREAMS; ++i) {
-    Lane &c = S->lanes[i];
-    if (c.busy && cudaEventQuery(c.done) == cudaSuccess) c.busy = false;
-    if (!c.busy && !L) L = &c;
-  }
-  if (!L) return MVP_OK;  // launched when a stream frees up (next submit or poll)
-  int n = 0, tiles = 0;
-  for (auto &kv : S->inflight) {
-    InFlight &f = kv.second;
-    if (f.launched) continue;
-    const mvp_request &q = f.req;
-    const Avatar &A = S->avatars[q.avatar];
-    mvp::BatchReq &B = L->h_reqs[n++];
-    memset(&B, 0, sizeof(B));
-    B.seq = f.seq;
-    B.slot = f.slot;
-    B.tile_begin = tiles;
-    B.n_tiles = warp_tiles(q.width, q.height);
-    B.n_prims = A.prims.n;
-    B.M = A.prims.M;
-    B.dtype = A.prims.dtype;
-    B.n_steps = (int)mvp_num_steps(q.t_near, q.t_far, q.dt);
-    B.width = q.width;
-    B.height = q.height;
-    B.payload = A.prims.payload;
-    B.nodes = A.bvh.nodes;
-    B.pose = A.bvh.pose;
-    B.xf = A.bvh.xf;
-    B.out = reinterpret_cast<float *>(S->arena_base + f.off);
-    memcpy(B.c2w, q.c2w, sizeof(B.c2w));
-    B.focal = q.focal;
-    B.t_near = q.t_near;
-    B.t_far = q.t_far;
-    B.dt = q.dt;
-    B.stop_T = (float)(1.0 - (double)q.eps_early);
-    memcpy(B.bg, q.bg, sizeof(B.bg));
-    tiles += B.n_tiles;
-    f.launched = true;
-  }
-  cudaError_t e = cudaMemcpyAsync(L->d_reqs, L->h_reqs, sizeof(mvp::BatchReq) * n, cudaMemcpyHostToDevice, L->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(L->d_counters, 0, sizeof(unsigned int) * (n + 1), L->stream);
-  if (e != cudaSuccess) return serve_fail(MVP_ERR_CUDA, cudaGetErrorString(e));
-  mvp::BatchArgs a;
-  a.reqs = L->d_reqs;
-  a.n_req = n;
-  a.total_tiles = tiles;
-  a.claimed = L->d_counters;
-  a.tiles_done = L->d_counters + 1;
-  a.done = S->d_done;
-  a.status = S->d_status;
-  int grid = S->grid;
-  const int need = (tiles + mvp::TILE_WARPS - 1) / mvp::TILE_WARPS;
-  if (need < grid) grid = need;
-  mvp::k_serve<<<grid, mvp::TILE_WARPS * 32, S->smem, L->stream>>>(a);
-  e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaEventRecord(L->done, L->stream);
-  if (e != cudaSuccess) return serve_fail(MVP_ERR_CUDA, cudaGetErrorString(e));
-  L->busy = true;
-  S->batches++;
   return MVP_OK;
 }
 
@@ -436,23 +345,18 @@ mvp_status mvp_serve_create(mvp_ctx *ctx, size_t hbm_budget, int32_t max_slots, 
   S->d_done = reinterpret_cast<mvp::ReqDone *>(d);
   if ((e = cudaMalloc(&S->d_status, 256)) != cudaSuccess) return bail("status word");
   if ((e = cudaMemset(S->d_status, 0, 256)) != cudaSuccess) return bail("status reset");
-  for (int i = 0; i < mvp::SERVE_STREAMS; ++i) {
-    Lane &L = S->lanes[i];
-    if ((e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking)) != cudaSuccess) return bail("stream");
-    if ((e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming)) != cudaSuccess) return bail("event");
-    if ((e = cudaHostAlloc(&L.h_reqs, sizeof(mvp::BatchReq) * max_slots, cudaHostAllocDefault)) != cudaSuccess)
-      return bail("batch staging");
-    if ((e = cudaMalloc(&L.d_reqs, sizeof(mvp::BatchReq) * max_slots)) != cudaSuccess) return bail("batch table");
-    if ((e = cudaMalloc(&L.d_counters, sizeof(unsigned int) * (max_slots + 1))) != cudaSuccess)
-      return bail("batch counters");
-  }
+  if ((e = cudaMalloc(&S->d_tiles_done, sizeof(unsigned int) * max_slots)) != cudaSuccess) return bail("tile counters");
+  if ((e = cudaMemset(S->d_tiles_done, 0, sizeof(unsigned int) * max_slots)) != cudaSuccess)
+    return bail("tile counter reset");
+  for (cudaStream_t &st : S->streams)
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return bail("stream");
   if ((e = cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking)) != cudaSuccess) return bail("copy stream");
-  S->smem = (sizeof(mvp::TileShared<mvp::SERVE_CAP>) + sizeof(mvp::BatchReq)) * mvp::TILE_WARPS;
-  if ((e = cudaFuncSetAttribute(mvp::k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem)) !=
-      cudaSuccess)
-    return bail("kernel attribute");
+  S->smem = sizeof(mvp::TileShared<mvp::SERVE_CAP>) * mvp::TILE_WARPS;
+  for (mvp::ServeKernel k : mvp::k_serve_table)
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem)) != cudaSuccess)
+      return bail("kernel attribute");
   int per_sm = 0, sms = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mvp::k_serve, mvp::TILE_WARPS * 32, S->smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mvp::k_serve_table[0], mvp::TILE_WARPS * 32, S->smem);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   S->grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   *out = S;
@@ -462,20 +366,16 @@ mvp_status mvp_serve_create(mvp_ctx *ctx, size_t hbm_budget, int32_t max_slots, 
 void mvp_serve_destroy(mvp_server *S) {
   if (!S) return;
   cudaSetDevice(S->device);
-  for (auto &L : S->lanes)
-    if (L.stream) cudaStreamSynchronize(L.stream);
+  for (cudaStream_t st : S->streams)
+    if (st) cudaStreamSynchronize(st);
   if (S->copy) cudaStreamSynchronize(S->copy);
   for (auto &a : S->avatars) mvp::bvh_release(a.bvh);
   if (S->arena_base) cudaFree(S->arena_base);
   if (S->d_status) cudaFree(S->d_status);
   if (S->h_done) cudaFreeHost(S->h_done);
-  for (auto &L : S->lanes) {
-    if (L.h_reqs) cudaFreeHost(L.h_reqs);
-    if (L.d_reqs) cudaFree(L.d_reqs);
-    if (L.d_counters) cudaFree(L.d_counters);
-    if (L.done) cudaEventDestroy(L.done);
-    if (L.stream) cudaStreamDestroy(L.stream);
-  }
+  if (S->d_tiles_done) cudaFree(S->d_tiles_done);
+  for (cudaStream_t st : S->streams)
+    if (st) cudaStreamDestroy(st);
   if (S->copy) cudaStreamDestroy(S->copy);
   delete S;
 }
@@ -549,7 +449,7 @@ mvp_status mvp_serve_poll(mvp_server *S, uint64_t ticket, float *out_rgba, doubl
     return serve_fail(MVP_ERR_INVALID_ARG, "unknown ticket");
   }
   InFlight f = it->second;
-  if (!f.launched || !is_done(S, f)) {
+  if (!is_done(S, f)) {
     mvp_status st = pump(S);
     return st ? st : MVP_NOT_READY;
   }
@@ -562,6 +462,7 @@ mvp_status mvp_serve_poll(mvp_server *S, uint64_t ticket, float *out_rgba, doubl
   if (latency_ms) *latency_ms = ms;
   S->arena.release(f.off, f.bytes);
   S->inflight_bytes -= f.bytes;
+  S->outstanding[f.stream]--;
   S->slot_busy[f.slot] = false;
   S->inflight.erase(it);
   S->completed++;
@@ -596,7 +497,7 @@ mvp_status mvp_serve_stats(mvp_server *S, mvp_serve_info *info) {
   cudaMemcpyAsync(&st, S->d_status, sizeof(int), cudaMemcpyDeviceToHost, S->copy);
   cudaStreamSynchronize(S->copy);
   info->device_status = st;
-  info->batches = (int64_t)S->batches;
+  info->batches = (int64_t)S->launches;
   return MVP_OK;
 }
 

@@ -1,4 +1,4 @@
-"""Serving (continuous batching through one persistent kernel).
+"""Serving (continuous batching: one launch per admitted request, requests overlapping on the GPU).
 
 Each request's image must equal mvp_camera_rays + mvp_raymarch_fwd on the same
 avatar, and must be the same whether the request runs alone or in a mix of many
