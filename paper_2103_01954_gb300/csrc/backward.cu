@@ -123,10 +123,12 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
             c111 = Voxel<DT>::load(pbase, vo + M2 + M + 1);
             held = vo;
           }
-          const float4 c00 = lerp4(c000, c001, fx), c01 = lerp4(c010, c011, fx);
-          const float4 c10 = lerp4(c100, c101, fx), c11 = lerp4(c110, c111, fx);
-          const float4 c0 = lerp4(c00, c01, fy), c1 = lerp4(c10, c11, fy);
-          const float4 val = lerp4(c0, c1, fz);
+          // the forward march's interpolation, rounding for rounding
+          const float2 wx = splat2(fx), nwx = splat2(-fx), wy = splat2(fy), nwy = splat2(-fy);
+          const float4 c00 = lerp4x2(c000, c001, wx, nwx), c01 = lerp4x2(c010, c011, wx, nwx);
+          const float4 c10 = lerp4x2(c100, c101, wx, nwx), c11 = lerp4x2(c110, c111, wx, nwx);
+          const float4 c0 = lerp4x2(c00, c01, wy, nwy), c1 = lerp4x2(c10, c11, wy, nwy);
+          const float4 val = lerp4x2(c0, c1, splat2(fz), splat2(-fz));
           const bool at_clamp = i == i_clamp;
           const float ga = at_clamp ? ga_s : ga_pre;
           const float gr = at_clamp ? gsr : gcr, gg = at_clamp ? gsg : gcg, gb = at_clamp ? gsb : gcb;

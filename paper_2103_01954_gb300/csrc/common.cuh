@@ -199,6 +199,19 @@ __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float w) {
                      fmaf(w, b.w - a.w, a.w));
 }
 
+// Packed FP32x2 arithmetic (two FP32 FMAs per instruction on sm_100 and later).
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 splat2(float v) { return make_float2(v, v); }
+
+// (1 - w) a + w b per component as fma(w, b, fma(-w, a, a)) on packed pairs; exact at
+// w = 0 and w = 1. w2 = (w, w), nw2 = (-w, -w).
+__device__ __forceinline__ float4 lerp4x2(float4 a, float4 b, float2 w2, float2 nw2) {
+  const float2 l = __ffma2_rn(w2, lo2(b), __ffma2_rn(nw2, lo2(a), lo2(a)));
+  const float2 h = __ffma2_rn(w2, hi2(b), __ffma2_rn(nw2, hi2(a), hi2(a)));
+  return make_float4(l.x, l.y, h.x, h.y);
+}
+
 __device__ __forceinline__ float warp_min(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(FULL, v, o));

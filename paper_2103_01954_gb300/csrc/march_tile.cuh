@@ -27,29 +27,6 @@ struct VoxelBytes {
   static constexpr int value = DT == MVP_F32 ? 16 : 8;
 };
 
-// Gather the 8 voxels of the cell at (ix, iy, iz) of one primitive's payload and
-// interpolate RGBA. MT > 0 makes the payload edge a compile-time constant, so the
-// eight addresses are immediate offsets from one base.
-template <int DT, int MT>
-__device__ __forceinline__ float4 trilinear(const char *base, int Mr, int ix, int iy, int iz, float fx, float fy,
-                                            float fz) {
-  const int M = MT > 0 ? MT : Mr;
-  const int o = (iz * M + iy) * M + ix;
-  const void *p = base;
-  const float4 c000 = Voxel<DT>::load(p, o);
-  const float4 c001 = Voxel<DT>::load(p, o + 1);
-  const float4 c010 = Voxel<DT>::load(p, o + M);
-  const float4 c011 = Voxel<DT>::load(p, o + M + 1);
-  const float4 c100 = Voxel<DT>::load(p, o + M * M);
-  const float4 c101 = Voxel<DT>::load(p, o + M * M + 1);
-  const float4 c110 = Voxel<DT>::load(p, o + M * M + M);
-  const float4 c111 = Voxel<DT>::load(p, o + M * M + M + 1);
-  const float4 c00 = lerp4(c000, c001, fx), c01 = lerp4(c010, c011, fx);
-  const float4 c10 = lerp4(c100, c101, fx), c11 = lerp4(c110, c111, fx);
-  const float4 c0 = lerp4(c00, c01, fy), c1 = lerp4(c10, c11, fy);
-  return lerp4(c0, c1, fz);
-}
-
 // March one warp tile whose lane ray is L (L.r < 0: no ray). Writes the output
 // (and the adjoint state / evaluation count) of each lane's ray. A single sample
 // overlapped by more than CAP primitives sets STATUS_CAPACITY in a.status.
@@ -105,11 +82,12 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
         xs[c][1] = fmaf(ti, L.d[1], L.o[1]);
         xs[c][2] = fmaf(ti, L.d[2], L.o[2]);
       }
-      float sa[MARCH_CHUNK], sr[MARCH_CHUNK], sg[MARCH_CHUNK], sb[MARCH_CHUNK];
+      // per sample: (sum alpha*r, sum alpha*g) and (sum alpha*b, sum alpha), packed pairs
+      float2 srg[MARCH_CHUNK], sba[MARCH_CHUNK];
       int ne_c[MARCH_CHUNK];  // evaluations per sample (count variant)
 #pragma unroll
       for (int c = 0; c < MARCH_CHUNK; ++c) {
-        sa[c] = sr[c] = sg[c] = sb[c] = 0.0f;
+        srg[c] = sba[c] = make_float2(0.0f, 0.0f);
         ne_c[c] = 0;
       }
       uint32_t b0 = m0, b1 = m1;
@@ -151,14 +129,14 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
             held = v;
           }
           const float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
-          const float4 c00 = lerp4(c000, c001, fx), c01 = lerp4(c010, c011, fx);
-          const float4 c10 = lerp4(c100, c101, fx), c11 = lerp4(c110, c111, fx);
-          const float4 q0 = lerp4(c00, c01, fy), q1 = lerp4(c10, c11, fy);
-          const float4 val = lerp4(q0, q1, fz);
-          sa[c] += val.w;
-          sr[c] = fmaf(val.w, val.x, sr[c]);
-          sg[c] = fmaf(val.w, val.y, sg[c]);
-          sb[c] = fmaf(val.w, val.z, sb[c]);
+          const float2 wx = splat2(fx), nwx = splat2(-fx), wy = splat2(fy), nwy = splat2(-fy);
+          const float2 wz = splat2(fz), nwz = splat2(-fz);
+          const float4 c00 = lerp4x2(c000, c001, wx, nwx), c01 = lerp4x2(c010, c011, wx, nwx);
+          const float4 c10 = lerp4x2(c100, c101, wx, nwx), c11 = lerp4x2(c110, c111, wx, nwx);
+          const float4 q0 = lerp4x2(c00, c01, wy, nwy), q1 = lerp4x2(c10, c11, wy, nwy);
+          const float4 val = lerp4x2(q0, q1, wz, nwz);
+          srg[c] = __ffma2_rn(splat2(val.w), lo2(val), srg[c]);
+          sba[c] = __ffma2_rn(make_float2(val.w, 1.0f), hi2(val), sba[c]);
           if (COUNT) ++ne_c[c];
         }
       }
@@ -168,8 +146,8 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
         if (!alive || ii >= ie) continue;
         if (COUNT) n_eval += ne_c[c];  // samples past a ray's termination are not counted
         // clamped additive accumulation: w = min(a, 1 - T), I += c w / a, T += w
-        const float aa = sa[c] * a.dt;
-        const float cr = sr[c] * a.dt, cg = sg[c] * a.dt, cb = sb[c] * a.dt;
+        const float aa = sba[c].y * a.dt;
+        const float cr = srg[c].x * a.dt, cg = srg[c].y * a.dt, cb = sba[c].x * a.dt;
         const float rem = 1.0f - T;
         if (aa <= rem) {
           Ir += cr;
