@@ -132,6 +132,54 @@ __device__ __forceinline__ bool packet_hits_box(const Packet &P, float4 a, float
   return tmin <= tmax + 1.0e-5f * (fabsf(tmax) + fabsf(tmin)) + 1.0e-30f;
 }
 
+// Can some ray of the packet meet the primitive's oriented box for t in [ta, tb]?
+// A conservative interval test in the box's frame: the packet's origin and
+// direction boxes map to intervals o' +- ro, d' +- rd per local axis (centre times
+// R^T, radius times |R^T|, then scaled by 1/s). For t >= 0 the local coordinate
+// o + t d of any packet ray lies in [lo_o + t lo_d, hi_o + t hi_d], so each axis
+// bounds t by two linear inequalities against the slab [-1, 1]. Radii are widened
+// by 1e-5 of the magnitudes involved and the slab by 1e-4, far above FP32 rounding,
+// so a primitive that the exact FP32 slab test of any packet ray accepts passes.
+__device__ __forceinline__ bool packet_hits_obb(const Packet &P, const Pose &K, float ta, float tb) {
+  if (!(ta >= 0.0f)) return true;  // the interval form below assumes t >= 0
+  const float R[9] = {K.p0.x, K.p0.y, K.p0.z, K.p0.w, K.p1.x, K.p1.y, K.p1.z, K.p1.w, K.p2.x};
+  const float tk[3] = {K.p2.y, K.p2.z, K.p2.w};
+  const float is[3] = {K.p3.x, K.p3.y, K.p3.z};
+  float pc[3], pr[3], pm[3], dc[3], dr[3], dm[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    pc[i] = 0.5f * (P.omin[i] + P.omax[i]) - tk[i];
+    pr[i] = 0.5f * (P.omax[i] - P.omin[i]);
+    pm[i] = fabsf(P.omin[i]) + fabsf(P.omax[i]) + fabsf(tk[i]);
+    dc[i] = 0.5f * (P.dmin[i] + P.dmax[i]);
+    dr[i] = 0.5f * (P.dmax[i] - P.dmin[i]);
+    dm[i] = fabsf(P.dmin[i]) + fabsf(P.dmax[i]);
+  }
+  constexpr float B = 1.0f + 1.0e-4f;
+  float tmin = ta, tmax = tb;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float a0 = R[j], a1 = R[3 + j], a2 = R[6 + j];
+    const float b0 = fabsf(a0), b1 = fabsf(a1), b2 = fabsf(a2);
+    const float oc = is[j] * fmaf(a2, pc[2], fmaf(a1, pc[1], a0 * pc[0]));
+    const float ro = is[j] * (fmaf(b2, pr[2], fmaf(b1, pr[1], b0 * pr[0])) +
+                              1.0e-5f * fmaf(b2, pm[2], fmaf(b1, pm[1], b0 * pm[0])));
+    const float ddc = is[j] * fmaf(a2, dc[2], fmaf(a1, dc[1], a0 * dc[0]));
+    const float rd = is[j] * (fmaf(b2, dr[2], fmaf(b1, dr[1], b0 * dr[0])) +
+                              1.0e-5f * fmaf(b2, dm[2], fmaf(b1, dm[1], b0 * dm[0])));
+    const float lo_o = oc - ro, hi_o = oc + ro, lo_d = ddc - rd, hi_d = ddc + rd;
+    // lo_o + t lo_d <= B
+    if (lo_d > 0.0f) tmax = fminf(tmax, (B - lo_o) / lo_d);
+    else if (lo_d < 0.0f) tmin = fmaxf(tmin, (B - lo_o) / lo_d);
+    else if (lo_o > B) return false;
+    // hi_o + t hi_d >= -B
+    if (hi_d < 0.0f) tmax = fminf(tmax, (-B - hi_o) / hi_d);
+    else if (hi_d > 0.0f) tmin = fmaxf(tmin, (-B - hi_o) / hi_d);
+    else if (hi_o < -B) return false;
+  }
+  return tmin <= tmax + 1.0e-5f * (fabsf(tmin) + fabsf(tmax)) + 1.0e-30f;
+}
+
 // Warp-private shared memory of a tile. The packet bounds are warp-uniform, so
 // they live here rather than in every lane's registers.
 template <int CAP>
@@ -236,7 +284,35 @@ __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__r
   bool live = L.r >= 0 && lane_last >= w0;
   int hi_cap = min(w1 - 1, lane_last);
   const float inv_dt = 1.0f / dt;
+  // the packet tests use the window's time range with a small slack
+  const float slack = 1.0e-5f * (fabsf(ta) + fabsf(tb)) + 1.0e-30f;
   auto emit = [&](int nc) -> bool {
+    // drop candidates whose oriented box no packet ray can meet in the window (one
+    // candidate per lane), keeping the survivors in traversal order
+    {
+      int kept = 0;
+      for (int c0 = 0; c0 < nc; c0 += 32) {
+        const int c = c0 + lane;
+        int k = -1;
+        bool keep = false;
+        if (c < nc) {
+          k = sh.cand[c];
+          const float4 *qa = reinterpret_cast<const float4 *>(pose + k);
+          Pose Pk;
+          Pk.p0 = __ldg(qa);
+          Pk.p1 = __ldg(qa + 1);
+          Pk.p2 = __ldg(qa + 2);
+          Pk.p3 = __ldg(qa + 3);
+          keep = packet_hits_obb(sh.pk, Pk, ta - slack, tb + slack);
+        }
+        const unsigned m = __ballot_sync(FULL, keep);
+        __syncwarp();  // every lane has read its candidate before any is overwritten
+        if (keep) sh.cand[kept + __popc(m & ((1u << lane) - 1u))] = k;
+        kept += __popc(m);
+        __syncwarp();
+      }
+      nc = kept;
+    }
     for (int c = 0; c < nc; ++c) {
       if ((c & 31) == 0 && c + lane < nc) {
         // pull the next 32 candidates' poses (one 64-byte line each) into L1 at once,
@@ -277,8 +353,6 @@ __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__r
     }
     return true;
   };
-  // the packet test uses the window's time range with a small slack
-  float slack = 1.0e-5f * (fabsf(ta) + fabsf(tb)) + 1.0e-30f;
   bool ok = traverse_tile(sh, nodes, n_prims, ta - slack, tb + slack, emit);
   __syncwarp();
   if (!ok) return -1;
