@@ -115,47 +115,48 @@ __device__ __forceinline__ float sample_t(float t_near, float dt, int i) {
 }
 
 // Smallest i in [0, n] with t_i >= v (n if none). t_i is non-decreasing in i. The
-// estimate (v - t_near) * (1/dt) is only a starting point: the loops below make the
-// result exact against the sample times themselves.
-__device__ __forceinline__ int first_sample_geq(float v, float t_near, float dt, float inv_dt, int n) {
-  float x = (v - t_near) * inv_dt;
-  int i;
-  if (!(x > 0.0f)) i = 0;
-  else if (x >= (float)n) i = n;
-  else i = (int)ceilf(x);
+// estimate (v - t_near) * (1/dt) is only a starting point. The four sample times
+// around it settle, without branches, every case where it is off by at most one
+// (t_{i-1} >= v moves down, t_i < v moves up); anything else takes the exact walk.
+static __device__ __noinline__ int first_sample_walk(float v, float t_near, float dt, int n, int i, bool strict) {
+  // strict: smallest i with t_i > v; else with t_i >= v
+  auto after = [&](int j) { const float tj = sample_t(t_near, dt, j); return strict ? tj > v : tj >= v; };
   int it = 0;
-  while (i > 0 && sample_t(t_near, dt, i - 1) >= v && it < 64) { --i; ++it; }
-  while (i < n && sample_t(t_near, dt, i) < v && it < 128) { ++i; ++it; }
+  while (i > 0 && after(i - 1) && it < 64) { --i; ++it; }
+  while (i < n && !after(i) && it < 128) { ++i; ++it; }
   if (it >= 64) {  // estimate far off (huge t_near relative to dt): bisect
     int lo = 0, hi = n;
     while (lo < hi) {
-      int mid = (lo + hi) >> 1;
-      if (sample_t(t_near, dt, mid) >= v) hi = mid; else lo = mid + 1;
+      const int mid = (lo + hi) >> 1;
+      if (after(mid)) hi = mid; else lo = mid + 1;
     }
     i = lo;
   }
   return i;
 }
 
+__device__ __forceinline__ int first_sample_settle(float v, float t_near, float dt, int n, int i, bool strict) {
+  const float sm2 = sample_t(t_near, dt, max(i - 2, 0)), sm1 = sample_t(t_near, dt, max(i - 1, 0));
+  const float s0 = sample_t(t_near, dt, min(i, n)), sp1 = sample_t(t_near, dt, min(i + 1, n));
+  const bool m1 = i > 0 && (strict ? sm1 > v : sm1 >= v);       // answer <= i - 1
+  const bool m2 = i > 1 && (strict ? sm2 > v : sm2 >= v);       // answer <= i - 2
+  const bool p0 = i < n && !(strict ? s0 > v : s0 >= v);        // answer >= i + 1
+  const bool p1 = i + 1 < n && !(strict ? sp1 > v : sp1 >= v);  // answer >= i + 2
+  if (!m2 && !p1) return m1 ? i - 1 : (p0 ? i + 1 : i);
+  return first_sample_walk(v, t_near, dt, n, i, strict);
+}
+
+__device__ __forceinline__ int first_sample_geq(float v, float t_near, float dt, float inv_dt, int n) {
+  const float x = (v - t_near) * inv_dt;
+  const int i = !(x > 0.0f) ? 0 : (x >= (float)n ? n : (int)ceilf(x));
+  return first_sample_settle(v, t_near, dt, n, i, false);
+}
+
 // Smallest i in [0, n] with t_i > v (n if none).
 __device__ __forceinline__ int first_sample_gt(float v, float t_near, float dt, float inv_dt, int n) {
-  float x = (v - t_near) * inv_dt;
-  int i;
-  if (x < 0.0f) i = 0;
-  else if (x >= (float)n) i = n;
-  else i = (int)floorf(x) + 1;
-  int it = 0;
-  while (i > 0 && sample_t(t_near, dt, i - 1) > v && it < 64) { --i; ++it; }
-  while (i < n && sample_t(t_near, dt, i) <= v && it < 128) { ++i; ++it; }
-  if (it >= 64) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-      int mid = (lo + hi) >> 1;
-      if (sample_t(t_near, dt, mid) > v) hi = mid; else lo = mid + 1;
-    }
-    i = lo;
-  }
-  return i;
+  const float x = (v - t_near) * inv_dt;
+  const int i = x < 0.0f ? 0 : (x >= (float)n ? n : (int)floorf(x) + 1);
+  return first_sample_settle(v, t_near, dt, n, i, true);
 }
 
 // ---------------------------------------------------------------- payload loads

@@ -313,36 +313,14 @@ __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__r
       }
       nc = kept;
     }
-    for (int c = 0; c < nc; ++c) {
-      if ((c & 31) == 0 && c + lane < nc) {
-        // pull the next 32 candidates' poses (one 64-byte line each) into L1 at once,
-        // so the loads below do not wait on L2 one candidate after another
-        const Pose *pp = pose + sh.cand[c + lane];
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(pp));
-      }
-      const int k = sh.cand[c];
-      float4 pk[4];
-      const float4 *qa = reinterpret_cast<const float4 *>(pose + k);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) pk[j] = __ldg(qa + j);
-      Pose Pk;
-      Pk.p0 = pk[0];
-      Pk.p1 = pk[1];
-      Pk.p2 = pk[2];
-      Pk.p3 = pk[3];
-      int ilo = 1, ihi = 0;
-      if (live) {
-        float tin, tout;
-        if (slab_spec(Pk, L.o[0], L.o[1], L.o[2], L.d[0], L.d[1], L.d[2], t_near, t_far, tin, tout)) {
-          ilo = max(first_sample_geq(tin, t_near, dt, inv_dt, n_steps), w0);
-          ihi = min(first_sample_gt(tout, t_near, dt, inv_dt, n_steps) - 1, hi_cap);
-        }
-      }
-      bool has = ilo <= ihi;
-      if (__ballot_sync(FULL, has) == 0) continue;
+    // the exact per-lane test, two candidates at a time so that their dependency
+    // chains overlap; entries are appended in candidate order
+    auto append = [&](int k, int ilo, int ihi) -> bool {
+      const bool has = ilo <= ihi;
+      if (__ballot_sync(FULL, has) == 0) return true;
       if (ne >= CAP) return false;
-      int lo_min = __reduce_min_sync(FULL, has ? ilo : 0x7fffffff);
-      int hi_max = __reduce_max_sync(FULL, has ? ihi : -1);
+      const int lo_min = __reduce_min_sync(FULL, has ? ilo : 0x7fffffff);
+      const int hi_max = __reduce_max_sync(FULL, has ? ihi : -1);
       sh.erng[ne][lane] = has ? ((uint32_t)ilo | ((uint32_t)ihi << 16)) : EMPTY_RANGE;
       if (lane == 0) {
         sh.ek[ne] = k;
@@ -350,6 +328,34 @@ __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__r
         sh.ehi[ne] = hi_max;
       }
       ++ne;
+      return true;
+    };
+    for (int c = 0; c < nc; c += 2) {
+      const bool two = c + 1 < nc;
+      const int k0 = sh.cand[c], k1 = sh.cand[two ? c + 1 : c];
+      const float4 *q0 = reinterpret_cast<const float4 *>(pose + k0);
+      const float4 *q1 = reinterpret_cast<const float4 *>(pose + k1);
+      Pose P0, P1;
+      P0.p0 = __ldg(q0);
+      P1.p0 = __ldg(q1);
+      P0.p1 = __ldg(q0 + 1);
+      P1.p1 = __ldg(q1 + 1);
+      P0.p2 = __ldg(q0 + 2);
+      P1.p2 = __ldg(q1 + 2);
+      P0.p3 = __ldg(q0 + 3);
+      P1.p3 = __ldg(q1 + 3);
+      float tin0, tout0, tin1, tout1;
+      const bool h0 = slab_spec(P0, L.o[0], L.o[1], L.o[2], L.d[0], L.d[1], L.d[2], t_near, t_far, tin0, tout0) && live;
+      const bool h1 = slab_spec(P1, L.o[0], L.o[1], L.o[2], L.d[0], L.d[1], L.d[2], t_near, t_far, tin1, tout1) && live;
+      // lanes that miss search from t_near (a cheap, exact case) and discard the result
+      const float u0 = h0 ? tin0 : t_near, v0 = h0 ? tout0 : t_near;
+      const float u1 = h1 ? tin1 : t_near, v1 = h1 ? tout1 : t_near;
+      const int a0 = first_sample_geq(u0, t_near, dt, inv_dt, n_steps);
+      const int a1 = first_sample_geq(u1, t_near, dt, inv_dt, n_steps);
+      const int b0 = first_sample_gt(v0, t_near, dt, inv_dt, n_steps);
+      const int b1 = first_sample_gt(v1, t_near, dt, inv_dt, n_steps);
+      if (!append(k0, h0 ? max(a0, w0) : 1, h0 ? min(b0 - 1, hi_cap) : 0)) return false;
+      if (two && !append(k1, h1 ? max(a1, w0) : 1, h1 ? min(b1 - 1, hi_cap) : 0)) return false;
     }
     return true;
   };
