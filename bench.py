@@ -273,11 +273,84 @@ def _traffic(kernel_key: str):
     return None
 
 
+def _serve_trace(T, srv, ids, reqs, arrivals):
+    """Submit `reqs` at their Poisson arrival times and poll until all are done.
+    Returns (latencies in ms, wall seconds)."""
+    import time as _t
+
+    lat, pend = [], {}
+    t0 = _t.perf_counter()
+    j, n_req = 0, len(reqs)
+    while j < n_req or pend:
+        now = _t.perf_counter() - t0
+        while j < n_req and arrivals[j] <= now:
+            a, cam, w, h = reqs[j]
+            pend[srv.submit_raw(T.Server.request(ids[a], cam.matrix34(), cam.focal, w, h, 1.0, 5.0, 0.005))] = j
+            j += 1
+        for tk in list(pend):
+            st, ms = srv.poll(tk)
+            if st == 0:
+                lat.append(ms)
+                del pend[tk]
+    return lat, _t.perf_counter() - t0
+
+
+def _serving_budget_run(torch, T, synthetic, ctx, av_bf16, av_f32, seed):
+    """A 64 MB budget for images in flight on top of the 8 resident BF16 avatars: a
+    64-request burst is admitted as memory frees up (the rest waits, none is lost), an
+    extra FP32 avatar and a 4096x4096 request are refused (MVP_ERR_CAPACITY)."""
+    from paper_2103_01954_gb300 import binding as B
+
+    probe = T.Server(ctx, hbm_budget=100 * 10**9, max_slots=4)
+    for a in av_bf16:
+        probe.register(*a)
+    resident = probe.stats()["resident_bytes"]
+    probe.close()
+    budget = resident + (64 << 20)
+    srv = T.Server(ctx, hbm_budget=budget, max_slots=64)
+    ids = [srv.register(*a) for a in av_bf16]
+    refused_avatar = False
+    try:
+        srv.register(*av_f32[0])
+    except B.MVPError as e:
+        if e.status != B.MVP_ERR_CAPACITY:
+            raise
+        refused_avatar = True
+    rng = np.random.default_rng(seed + 64)
+    tks = []
+    for j in range(64):
+        w, h = synthetic.SERVE_RESOLUTIONS[j % 3]
+        cam = synthetic.random_camera(rng, 3.0, w, h, float(max(w, h)))
+        tks.append(srv.submit_raw(T.Server.request(ids[j % len(ids)], cam.matrix34(), cam.focal, w, h,
+                                                   1.0, 5.0, 0.005)))
+    pending_after_burst = srv.stats()["pending"]
+    refused_request = False
+    try:
+        srv.submit_raw(T.Server.request(ids[0], cam.matrix34(), 4096.0, 4096, 4096, 1.0, 5.0, 0.005))
+    except B.MVPError as e:
+        if e.status != B.MVP_ERR_CAPACITY:
+            raise
+        refused_request = True
+    done = 0
+    for tk in tks:
+        st, _ = srv.wait(tk, 60000.0)
+        done += int(st == 0)
+    st_ = srv.stats()
+    srv.close()
+    return {"hbm_budget": int(budget), "resident_bytes": int(resident), "image_budget": 64 << 20,
+            "extra_f32_avatar_refused": refused_avatar, "burst_requests": 64,
+            "pending_after_burst": int(pending_after_burst), "completed": done,
+            "max_in_flight": int(st_["max_in_flight"]), "request_4096x4096_refused": refused_request,
+            "device_status": int(st_["device_status"])}
+
+
 def _serving(torch, T, synthetic, rates, n_req, seed=0):
     """Poisson arrivals over 8 resident BF16 avatars (512x32^3 ... 32768x8^3), random
     cameras on the radius-3 sphere, resolutions {256x256, 512x512, 667x1024}; served
     with continuous batching (mvp_serve_*) and, on the same trace, one request at a
-    time with FP32 payloads (mvp_camera_rays + mvp_raymarch_fwd, synchronised)."""
+    time with FP32 payloads (mvp_camera_rays + mvp_raymarch_fwd, synchronised). At the
+    highest rate the same trace is also served with FP32 payloads; a 64 MB budget run
+    exercises refusal."""
     import time as _t
 
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -297,9 +370,10 @@ def _serving(torch, T, synthetic, rates, n_req, seed=0):
     srv = T.Server(ctx, hbm_budget=100 * 10**9, max_slots=64, arena_bytes=2 << 30)
     ids = [srv.register(*a) for a in av_bf16]
     resident = srv.stats()["resident_bytes"]
+    ids32 = [srv.register(*a) for a in av_f32]
     out_buf = torch.empty((1024 * 667, 4), dtype=torch.float32, device=dev)
     results = {}
-    for rate in rates:
+    for ri, rate in enumerate(rates):
         rng = np.random.default_rng(seed + int(rate))
         arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
         reqs = []
@@ -308,27 +382,14 @@ def _serving(torch, T, synthetic, rates, n_req, seed=0):
             w, h = synthetic.SERVE_RESOLUTIONS[int(rng.integers(0, 3))]
             cam = synthetic.random_camera(rng, 3.0, w, h, float(max(w, h)))
             reqs.append((a, cam, w, h))
+        rays = sum(w * h for _, _, w, h in reqs)
         # warm-up: a few requests so kernels and arenas are resident
         for a, cam, w, h in reqs[:4]:
-            tk = srv.submit_raw(T.Server.request(ids[a], cam.matrix34(), cam.focal, w, h, 1.0, 5.0, 0.005))
-            srv.wait(tk, 60000.0)
-        # continuous batching
-        lat, pend = [], {}
-        rays = sum(w * h for _, _, w, h in reqs)
-        t0 = _t.perf_counter()
-        j = 0
-        while j < n_req or pend:
-            now = _t.perf_counter() - t0
-            while j < n_req and arrivals[j] <= now:
-                a, cam, w, h = reqs[j]
-                pend[srv.submit_raw(T.Server.request(ids[a], cam.matrix34(), cam.focal, w, h, 1.0, 5.0, 0.005))] = j
-                j += 1
-            for tk in list(pend):
-                st, ms = srv.poll(tk)
-                if st == 0:
-                    lat.append(ms)
-                    del pend[tk]
-        wall = _t.perf_counter() - t0
+            for table in (ids, ids32):
+                tk = srv.submit_raw(T.Server.request(table[a], cam.matrix34(), cam.focal, w, h, 1.0, 5.0, 0.005))
+                srv.wait(tk, 60000.0)
+        # continuous batching, BF16 payloads
+        lat, wall = _serve_trace(T, srv, ids, reqs, arrivals)
         st_ = srv.stats()
         # one request at a time, FP32 payloads, same trace
         lat1 = []
@@ -345,18 +406,25 @@ def _serving(torch, T, synthetic, rates, n_req, seed=0):
             lat1.append((_t.perf_counter() - t0 - arrivals[k]) * 1e3)
         wall1 = _t.perf_counter() - t0
         ctx.sync()
-        results[f"{rate}_req_per_s"] = {
-            "requests": n_req, "p50_ms": round(float(np.percentile(lat, 50)), 3),
-            "p99_ms": round(float(np.percentile(lat, 99)), 3), "mrays_per_s": round(rays / wall / 1e6, 2),
-            "max_in_flight": int(st_["max_in_flight"]), "device_status": int(st_["device_status"]),
-            "one_at_a_time_f32": {"p50_ms": round(float(np.percentile(lat1, 50)), 3),
-                                  "p99_ms": round(float(np.percentile(lat1, 99)), 3),
-                                  "mrays_per_s": round(rays / wall1 / 1e6, 2)}}
+        r = {"requests": n_req, "p50_ms": round(float(np.percentile(lat, 50)), 3),
+             "p99_ms": round(float(np.percentile(lat, 99)), 3), "mrays_per_s": round(rays / wall / 1e6, 2),
+             "max_in_flight": int(st_["max_in_flight"]), "device_status": int(st_["device_status"]),
+             "one_at_a_time_f32": {"p50_ms": round(float(np.percentile(lat1, 50)), 3),
+                                   "p99_ms": round(float(np.percentile(lat1, 99)), 3),
+                                   "mrays_per_s": round(rays / wall1 / 1e6, 2)}}
+        if ri == len(rates) - 1:
+            # the same trace through the same server with FP32 payloads
+            lat32, wall32 = _serve_trace(T, srv, ids32, reqs, arrivals)
+            r["served_f32_payload"] = {"p50_ms": round(float(np.percentile(lat32, 50)), 3),
+                                       "p99_ms": round(float(np.percentile(lat32, 99)), 3),
+                                       "mrays_per_s": round(rays / wall32 / 1e6, 2)}
+        results[f"{rate}_req_per_s"] = r
     srv.close()
+    budget_run = _serving_budget_run(torch, T, synthetic, ctx, av_bf16, av_f32, seed)
     return {"avatars": [f"{n}x{M}^3" for n, M, _ in synthetic.AVATARS], "payload": "bf16",
             "resident_bytes": int(resident), "hbm_budget": 100 * 10**9,
             "resolutions": ["256x256", "512x512", "667x1024"], "latency": "host time from submit to completion seen",
-            "rates": results}
+            "rates": results, "budget_64MB_images": budget_run}
 
 
 def run_gpu(args):
@@ -523,8 +591,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="headline figure only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--serving-requests", type=int, default=400, help="requests per arrival rate (0: skip)")
-    ap.add_argument("--serving-rates", default="50,200,400,1600", help="Poisson arrival rates, requests/s")
+    ap.add_argument("--serving-requests", type=int, default=1000, help="requests per arrival rate (0: skip)")
+    ap.add_argument("--serving-rates", default="50,100,200,400,1600", help="Poisson arrival rates, requests/s")
     ap.add_argument("--serving-only", action="store_true", help="run only the serving measurement")
     ap.add_argument("--profile", action="store_true", help="render --frames frames of --workload, no timing")
     ap.add_argument("--workload", default=WORKLOAD)

@@ -62,20 +62,24 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
   const int64_t prim_bytes = (int64_t)M2 * M * VB;
   const int max_last = __reduce_max_sync(FULL, i_last);
 
-  int w0 = 0, wlen = a.n_steps;
+  int w0 = 0, wlen = a.n_steps, skip = 0;
   while (w0 <= max_last) {
     int w1 = min(a.n_steps, w0 + wlen);
     int ne = build_window<CAP>(sh, a.nodes, a.pose, a.xf, reinterpret_cast<const char *>(a.payload), prim_bytes,
-                               a.n_prims, L, valid ? i_last : -1, a.t_near, a.t_far, a.dt, a.n_steps, w0, w1);
-    if (ne < 0) {
-      if (w1 - w0 == 1) {
-        if (lane == 0) atomicOr(a.status, STATUS_CAPACITY);
-        return;
-      }
+                               a.n_prims, L, valid ? i_last : -1, a.t_near, a.t_far, a.dt, a.n_steps, w0, w1,
+                               skip);
+    if (ne == WINDOW_STACK) {
+      if (lane == 0) atomicOr(a.status, STATUS_CAPACITY);
+      return;
+    }
+    if (ne == WINDOW_FULL && w1 - w0 > 1) {  // split the depth range
       wlen = (w1 - w0 + 1) >> 1;
       continue;
     }
-    for (int e = 0; e < ne; ++e) {
+    // A one-sample window with more than CAP primitives is replayed in batches of
+    // CAP (entries are independent here): the next pass skips the ones done.
+    const int cnt = ne >= 0 ? ne : CAP;
+    for (int e = 0; e < cnt; ++e) {
       const int k = sh.ek[e];
       const Xform X = sh.exf[e];
       const void *pbase = sh.eptr[e];
@@ -193,6 +197,11 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
         }
       }
     }
+    if (ne == WINDOW_FULL) {
+      skip += CAP;
+      continue;
+    }
+    skip = 0;
     w0 = w1;
     wlen = min(a.n_steps, wlen * 2);
   }

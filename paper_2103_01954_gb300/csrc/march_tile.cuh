@@ -27,9 +27,85 @@ struct VoxelBytes {
   static constexpr int value = DT == MVP_F32 ? 16 : 8;
 };
 
+// Trilinear RGBA of one primitive (march transform X, payload at pbase) at world
+// point x: the arithmetic of the chunked loop in march_tile, rounding for rounding.
+template <int DT, int MT>
+__device__ __forceinline__ float4 sample_rgba(const Xform &X, const char *pbase, const float x[3], int Mr,
+                                              float Mm1) {
+  const int M = MT > 0 ? MT : Mr;
+  float ux = fmaf(X.r0.x, x[0], fmaf(X.r0.y, x[1], fmaf(X.r0.z, x[2], X.r0.w)));
+  float uy = fmaf(X.r1.x, x[0], fmaf(X.r1.y, x[1], fmaf(X.r1.z, x[2], X.r1.w)));
+  float uz = fmaf(X.r2.x, x[0], fmaf(X.r2.y, x[1], fmaf(X.r2.z, x[2], X.r2.w)));
+  ux = fminf(fmaxf(ux, 0.0f), Mm1);
+  uy = fminf(fmaxf(uy, 0.0f), Mm1);
+  uz = fminf(fmaxf(uz, 0.0f), Mm1);
+  const int ix = min((int)ux, M - 2), iy = min((int)uy, M - 2), iz = min((int)uz, M - 2);
+  const int v = (iz * M + iy) * M + ix;
+  const void *p = pbase;
+  const float4 c000 = Voxel<DT>::load(p, v), c001 = Voxel<DT>::load(p, v + 1);
+  const float4 c010 = Voxel<DT>::load(p, v + M), c011 = Voxel<DT>::load(p, v + M + 1);
+  const float4 c100 = Voxel<DT>::load(p, v + M * M), c101 = Voxel<DT>::load(p, v + M * M + 1);
+  const float4 c110 = Voxel<DT>::load(p, v + M * M + M), c111 = Voxel<DT>::load(p, v + M * M + M + 1);
+  const float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
+  const float2 wx = splat2(fx), nwx = splat2(-fx), wy = splat2(fy), nwy = splat2(-fy);
+  const float4 c00 = lerp4x2(c000, c001, wx, nwx), c01 = lerp4x2(c010, c011, wx, nwx);
+  const float4 c10 = lerp4x2(c100, c101, wx, nwx), c11 = lerp4x2(c110, c111, wx, nwx);
+  const float4 q0 = lerp4x2(c00, c01, wy, nwy), q1 = lerp4x2(c10, c11, wy, nwy);
+  return lerp4x2(q0, q1, splat2(fz), splat2(-fz));
+}
+
+// Sample w0 of every live lane against all primitives that contain it, evaluated
+// as one traversal of the tile finds them (no window list, so no limit on their
+// number): per lane the sums (alpha*r, alpha*g), (alpha*b, alpha) and the number
+// of evaluations. Membership is the window list's: the lane's exact sample range
+// of the primitive holds w0. Used when more than a window list's worth of
+// primitives meet one sample. Returns false on a traversal stack overflow.
+template <int DT, int MT, class SH>
+__device__ __forceinline__ bool sample_all(SH &sh, const MarchArgs &a, const LaneRay &L, bool live, int w0,
+                                           int M, float Mm1, int64_t prim_bytes, float2 &rg, float2 &ba,
+                                           int &nec) {
+  const float ti = sample_t(a.t_near, a.dt, w0);
+  const float inv_dt = 1.0f / a.dt;
+  const float xs[3] = {fmaf(ti, L.d[0], L.o[0]), fmaf(ti, L.d[1], L.o[1]), fmaf(ti, L.d[2], L.o[2])};
+  const char *payload = reinterpret_cast<const char *>(a.payload);
+  rg = ba = make_float2(0.0f, 0.0f);
+  nec = 0;
+  auto emit = [&](int nc) -> bool {
+    for (int c = 0; c < nc; ++c) {
+      const int k = sh.cand[c];
+      const float4 *q = reinterpret_cast<const float4 *>(a.pose + k);
+      Pose P;
+      P.p0 = __ldg(q);
+      P.p1 = __ldg(q + 1);
+      P.p2 = __ldg(q + 2);
+      P.p3 = __ldg(q + 3);
+      float tin, tout;
+      bool in = live && slab_spec(P, L.o[0], L.o[1], L.o[2], L.d[0], L.d[1], L.d[2], a.t_near, a.t_far, tin, tout);
+      if (in)
+        in = first_sample_geq(tin, a.t_near, a.dt, inv_dt, a.n_steps) <= w0 &&
+             w0 < first_sample_gt(tout, a.t_near, a.dt, inv_dt, a.n_steps);
+      if (!in) continue;
+      const float4 *xp = reinterpret_cast<const float4 *>(a.xf + k);
+      Xform X;
+      X.r0 = __ldg(xp);
+      X.r1 = __ldg(xp + 1);
+      X.r2 = __ldg(xp + 2);
+      const float4 val = sample_rgba<DT, MT>(X, payload + (int64_t)k * prim_bytes, xs, M, Mm1);
+      rg = __ffma2_rn(splat2(val.w), lo2(val), rg);
+      ba = __ffma2_rn(make_float2(val.w, 1.0f), hi2(val), ba);
+      ++nec;
+    }
+    return true;
+  };
+  const float slack = 2.0e-5f * fabsf(ti) + 1.0e-30f;
+  const bool ok = traverse_tile(sh, a.nodes, a.n_prims, ti - slack, ti + slack, emit);
+  __syncwarp();
+  return ok;
+}
+
 // March one warp tile whose lane ray is L (L.r < 0: no ray). Writes the output
-// (and the adjoint state / evaluation count) of each lane's ray. A single sample
-// overlapped by more than CAP primitives sets STATUS_CAPACITY in a.status.
+// (and the adjoint state / evaluation count) of each lane's ray. A traversal stack
+// overflow sets STATUS_CAPACITY in a.status; any number of primitives may overlap.
 template <int DT, int CAP, bool COUNT, int MT>
 __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs &a, const LaneRay &L) {
   const int lane = threadIdx.x & 31;
@@ -44,19 +120,71 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
   const float Mm1 = (float)(M - 1);
   const int64_t prim_bytes = (int64_t)M * M * M * VoxelBytes<DT>::value;
 
+  // Clamped additive accumulation of sample ii of a live lane with sums
+  // (sum alpha*r, sum alpha*g) and (sum alpha*b, sum alpha): w = min(a, 1 - T),
+  // I += c w / a, T += w.
+  auto composite = [&](float2 rg, float2 ba, int ii) {
+    const float aa = ba.y * a.dt;
+    const float cr = rg.x * a.dt, cg = rg.y * a.dt, cb = ba.x * a.dt;
+    const float rem = 1.0f - T;
+    if (aa <= rem) {
+      Ir += cr;
+      Ig += cg;
+      Ib += cb;
+      T = fminf(T + aa, 1.0f);
+      if (T >= a.stop_T) {
+        alive = false;
+        if (!COUNT && a.saved) {
+          Saved S = {0.0f, 0.0f, 0.0f, 0.0f, ii, -1};
+          a.saved[L.r] = S;
+        }
+        saved_done = true;
+      }
+    } else {
+      const float bt = rem / aa;
+      Ir = fmaf(cr, bt, Ir);
+      Ig = fmaf(cg, bt, Ig);
+      Ib = fmaf(cb, bt, Ib);
+      T = 1.0f;
+      alive = false;  // T = 1 >= 1 - eps_early
+      if (!COUNT && a.saved) {
+        Saved S = {cr / aa, cg / aa, cb / aa, bt, ii, ii};
+        a.saved[L.r] = S;
+      }
+      saved_done = true;
+    }
+  };
+
   int w0 = 0, wlen = a.n_steps;
+  bool stack_full = false;
   while (w0 < a.n_steps && __any_sync(FULL, alive)) {
     int w1 = min(a.n_steps, w0 + wlen);
     int lane_last = alive ? a.n_steps - 1 : -1;
     int ne = build_window<CAP>(sh, a.nodes, a.pose, a.xf, reinterpret_cast<const char *>(a.payload), prim_bytes,
                                a.n_prims, L, lane_last, a.t_near, a.t_far, a.dt, a.n_steps, w0, w1);
-    if (ne < 0) {
-      if (w1 - w0 == 1) {  // one sample overlapped by more than CAP primitives
-        if (lane == 0) atomicOr(a.status, STATUS_CAPACITY);
-        alive = false;
+    if (ne == WINDOW_STACK) {
+      stack_full = true;
+      break;
+    }
+    if (ne == WINDOW_FULL && w1 - w0 > 1) {  // split the depth range
+      wlen = (w1 - w0 + 1) >> 1;
+      continue;
+    }
+    if (ne == WINDOW_FULL) {
+      // more than CAP primitives meet this one sample in the tile: evaluate them as
+      // one traversal finds them, then composite
+      float2 rg, ba;
+      int nec;
+      if (!sample_all<DT, MT>(sh, a, L, alive, w0, M, Mm1, prim_bytes, rg, ba, nec)) {
+        stack_full = true;
         break;
       }
-      wlen = (w1 - w0 + 1) >> 1;
+      if (alive) {
+        if (COUNT) n_eval += nec;
+        composite(rg, ba, w0);
+      }
+      w0 = w1;
+      wlen = 2;
       continue;
     }
     // Samples go in chunks of MARCH_CHUNK: each window entry's transform is read from
@@ -145,42 +273,14 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
         const int ii = i + c;
         if (!alive || ii >= ie) continue;
         if (COUNT) n_eval += ne_c[c];  // samples past a ray's termination are not counted
-        // clamped additive accumulation: w = min(a, 1 - T), I += c w / a, T += w
-        const float aa = sba[c].y * a.dt;
-        const float cr = srg[c].x * a.dt, cg = srg[c].y * a.dt, cb = sba[c].x * a.dt;
-        const float rem = 1.0f - T;
-        if (aa <= rem) {
-          Ir += cr;
-          Ig += cg;
-          Ib += cb;
-          T = fminf(T + aa, 1.0f);
-          if (T >= a.stop_T) {
-            alive = false;
-            if (!COUNT && a.saved) {
-              Saved S = {0.0f, 0.0f, 0.0f, 0.0f, ii, -1};
-              a.saved[L.r] = S;
-            }
-            saved_done = true;
-          }
-        } else {
-          const float bt = rem / aa;
-          Ir = fmaf(cr, bt, Ir);
-          Ig = fmaf(cg, bt, Ig);
-          Ib = fmaf(cb, bt, Ib);
-          T = 1.0f;
-          alive = false;  // T = 1 >= 1 - eps_early
-          if (!COUNT && a.saved) {
-            Saved S = {cr / aa, cg / aa, cb / aa, bt, ii, ii};
-            a.saved[L.r] = S;
-          }
-          saved_done = true;
-        }
+        composite(srg[c], sba[c], ii);
       }
       i = ie;
     }
     w0 = w1;
     wlen = min(a.n_steps, wlen * 2);
   }
+  if (stack_full && lane == 0) atomicOr(a.status, STATUS_CAPACITY);
   if (!valid) return;
   if (COUNT) {
     a.n_eval[L.r] = n_eval;

@@ -19,6 +19,8 @@ constexpr int TILE_WARPS = 4;  // warps per block; a block covers 16x8 pixels
 constexpr int STACK = 256;     // traversal stack entries per warp
 constexpr int CBUF = 64;       // candidate leaves buffered per warp
 constexpr uint32_t EMPTY_RANGE = 0x0000ffffu;  // i_lo = 65535 > i_hi = 0
+constexpr int WINDOW_FULL = -1;   // build_window: more primitives than the list holds
+constexpr int WINDOW_STACK = -2;  // build_window: traversal stack overflow
 
 struct TileGeom {
   int64_t n_rays;
@@ -269,18 +271,22 @@ __device__ __forceinline__ void load_lane_ray(LaneRay &L, const float *__restric
 
 // Build the window's primitive list for samples [w0, w1): every traversal
 // candidate that some lane's exact slab interval meets at a sample of the window
-// with index <= lane_last (the lane's last live sample). Returns the number of
-// entries, or -1 if more than CAP are needed or the traversal stack overflowed.
+// with index <= lane_last (the lane's last live sample). The first `skip` such
+// primitives (in the fixed traversal order) are passed over. Returns the number of
+// entries; WINDOW_FULL if more than CAP remain after the skipped ones (the list
+// then holds the first CAP of them, ready to use); WINDOW_STACK if the traversal
+// stack overflowed.
 template <int CAP>
 __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__restrict__ nodes,
                                             const Pose *__restrict__ pose, const Xform *__restrict__ xf,
                                             const char *payload, int64_t prim_bytes, int n_prims,
                                             const LaneRay &L, int lane_last, float t_near, float t_far, float dt,
-                                            int n_steps, int w0, int w1) {
+                                            int n_steps, int w0, int w1, int skip = 0) {
   const int lane = threadIdx.x & 31;
   float ta = sample_t(t_near, dt, w0);
   float tb = sample_t(t_near, dt, w1 - 1);
-  int ne = 0;
+  int ne = 0, seen = 0;
+  bool full = false;
   bool live = L.r >= 0 && lane_last >= w0;
   int hi_cap = min(w1 - 1, lane_last);
   const float inv_dt = 1.0f / dt;
@@ -318,7 +324,11 @@ __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__r
     auto append = [&](int k, int ilo, int ihi) -> bool {
       const bool has = ilo <= ihi;
       if (__ballot_sync(FULL, has) == 0) return true;
-      if (ne >= CAP) return false;
+      if (seen++ < skip) return true;
+      if (ne >= CAP) {
+        full = true;
+        return false;
+      }
       const int lo_min = __reduce_min_sync(FULL, has ? ilo : 0x7fffffff);
       const int hi_max = __reduce_max_sync(FULL, has ? ihi : -1);
       sh.erng[ne][lane] = has ? ((uint32_t)ilo | ((uint32_t)ihi << 16)) : EMPTY_RANGE;
@@ -361,7 +371,7 @@ __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__r
   };
   bool ok = traverse_tile(sh, nodes, n_prims, ta - slack, tb + slack, emit);
   __syncwarp();
-  if (!ok) return -1;
+  if (!ok && !full) return WINDOW_STACK;
   // the entries' march transforms and payload pointers, loaded in parallel
   for (int e = lane; e < ne; e += 32) {
     const int k = sh.ek[e];
@@ -372,7 +382,7 @@ __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__r
     sh.eptr[e] = payload + (int64_t)k * prim_bytes;
   }
   __syncwarp();
-  return ne;
+  return ok ? ne : WINDOW_FULL;
 }
 
 // Active entries at sample i (two 32-bit masks) and the next sample at which the
