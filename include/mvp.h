@@ -163,8 +163,10 @@ MVP_API size_t mvp_saved_bytes(int64_t n_rays);
  * (device, mvp_saved_bytes(n) bytes, nullable) receives the per-ray state the
  * adjoint needs. `bvh` must have been built from the same prims. Rays are marched
  * by warps over 8x4 pixel tiles; each tile gathers at most 48 primitives at once
- * and splits its sample range when more overlap it. A single sample overlapped by
- * more than 48 primitives across one tile records MVP_ERR_CAPACITY. */
+ * and splits its sample range when more overlap it; a single sample met by more
+ * than 48 primitives across one tile is evaluated against all of them by an extra
+ * traversal. A traversal stack overflow (256 entries per tile) records
+ * MVP_ERR_CAPACITY. */
 MVP_API mvp_status mvp_raymarch_fwd(mvp_ctx *ctx, const mvp_prims *prims, const mvp_bvh *bvh,
                             const mvp_rays *rays, float *out_rgba, void *saved, mvp_stream stream);
 /* Same march, writing only the number of (sample, primitive) evaluations of each

@@ -206,9 +206,9 @@ mvp_status mvp_ctx_sync(mvp_ctx *ctx, mvp_stream stream) {
   if (st) {
     cudaMemset(ctx->d_status, 0, sizeof(int));
     if (st & mvp::STATUS_CAPACITY)
-      return fail(MVP_ERR_CAPACITY, "a kernel exceeded a capacity limit (more than %d primitives overlap one sample "
-                                    "of a ray tile, or the traversal stack of %d entries overflowed)",
-                  mvp::MARCH_CAP, mvp::STACK);
+      return fail(MVP_ERR_CAPACITY, "a kernel exceeded a capacity limit (a tile's BVH traversal stack of %d "
+                                    "entries overflowed)",
+                  mvp::STACK);
     return fail(MVP_ERR_DEVICE, "device status word 0x%x", st);
   }
   return ok();
