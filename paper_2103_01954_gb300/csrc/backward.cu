@@ -89,12 +89,17 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
       float acc[12];
 #pragma unroll
       for (int c = 0; c < 12; ++c) acc[c] = 0.0f;
-      const int e_lo = sh.elo[e], e_hi = sh.ehi[e];
+      // Each lane walks its own samples of the primitive from its own first one (the
+      // samples are independent here), so the warp loops max(count) times rather
+      // than over the union of the lanes' ranges.
+      const int cnt = max(hi - lo + 1, 0);
+      const int max_cnt = __reduce_max_sync(FULL, cnt);
       const int64_t kbase = (int64_t)k * M2 * M;
       int held = -1;  // voxel (within the primitive) whose cell corners are held
       float4 c000, c001, c010, c011, c100, c101, c110, c111;
-      for (int i = e_lo; i <= e_hi; ++i) {
-        const bool in = i >= lo && i <= hi;
+      for (int it = 0; it < max_cnt; ++it) {
+        const int i = lo + it;
+        const bool in = it < cnt;
         if (!in) continue;
         float fx = 0.0f, fy = 0.0f, fz = 0.0f;
         float4 gv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
