@@ -2,7 +2,8 @@
 // a data-parallel BVH every frame because the primitives move; it cites Karras'
 // construction from sorted Morton codes).
 //
-// Steps, all on one stream without host synchronisation:
+// Steps, all on one stream without host synchronisation (for n <= BVH_SORT1_N steps
+// 1-3 are k_prims_partial and the one-block k_sort_one instead):
 //   1. k_bounds   : min/max of the centres (one block; exact).
 //   2. k_prims    : rotation, membership pose, march transform, oriented-box world
 //                   bounds, 30-bit Morton code of the centre.
@@ -10,7 +11,8 @@
 //                   value (4 passes of 8 bits: count, scan, scatter).
 //   4. k_hierarchy: leaves and internal nodes of the binary radix tree over the
 //                   unique keys (morton << 32 | k), one thread per node.
-//   5. k_refit    : bottom-up union of child boxes with per-node arrival counters.
+//   5. refit      : each internal node's box as the union of the leaves in its sorted
+//                   range (k_refit_ranges), from 32- and 1024-leaf chunk unions.
 #include "bvh.cuh"
 
 namespace mvp {
@@ -68,12 +70,18 @@ __device__ __forceinline__ uint32_t quant10(float v, float lo, float hi) {
   return (uint32_t)f;
 }
 
-__global__ void k_prims(const float *__restrict__ t, const float *__restrict__ q, const float *__restrict__ s,
-                        int n, int M, const float *__restrict__ scene, Pose *__restrict__ pose,
-                        Xform *__restrict__ xf, float4 *__restrict__ pbox, uint32_t *__restrict__ keys,
-                        int *__restrict__ vals) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
+// 30-bit Morton code of centre k in the centres' bounds `scene`.
+__device__ __forceinline__ uint32_t morton_code(const float *__restrict__ t, int k, const float scene[6]) {
+  const uint32_t qx = quant10(t[3 * k], scene[0], scene[3]);
+  const uint32_t qy = quant10(t[3 * k + 1], scene[1], scene[4]);
+  const uint32_t qz = quant10(t[3 * k + 2], scene[2], scene[5]);
+  return (spread10(qx) << 2) | (spread10(qy) << 1) | spread10(qz);
+}
+
+// Pose, march transform and world box of primitive k.
+__device__ __forceinline__ void prim_setup(const float *__restrict__ t, const float *__restrict__ q,
+                                           const float *__restrict__ s, int k, int M, Pose *__restrict__ pose,
+                                           Xform *__restrict__ xf, float4 *__restrict__ pbox) {
   float tx = t[3 * k], ty = t[3 * k + 1], tz = t[3 * k + 2];
   float sx = s[3 * k], sy = s[3 * k + 1], sz = s[3 * k + 2];
   float R[9];
@@ -120,11 +128,47 @@ __global__ void k_prims(const float *__restrict__ t, const float *__restrict__ q
   }
   pbox[2 * k] = make_float4(lo[0], lo[1], lo[2], 0.0f);
   pbox[2 * k + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
-  uint32_t qx = quant10(tx, scene[0], scene[3]);
-  uint32_t qy = quant10(ty, scene[1], scene[4]);
-  uint32_t qz = quant10(tz, scene[2], scene[5]);
-  keys[k] = (spread10(qx) << 2) | (spread10(qy) << 1) | spread10(qz);
+}
+
+__global__ void k_prims(const float *__restrict__ t, const float *__restrict__ q, const float *__restrict__ s,
+                        int n, int M, const float *__restrict__ scene, Pose *__restrict__ pose,
+                        Xform *__restrict__ xf, float4 *__restrict__ pbox, uint32_t *__restrict__ keys,
+                        int *__restrict__ vals) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float sc[6] = {scene[0], scene[1], scene[2], scene[3], scene[4], scene[5]};
+  prim_setup(t, q, s, k, M, pose, xf, pbox);
+  keys[k] = morton_code(t, k, sc);
   vals[k] = k;
+}
+
+// Pose, march transform and world box of each primitive, and per block the bounds of
+// its centres (partial[block] = {lo xyz, hi xyz}) for the one-block sort to reduce.
+__global__ void __launch_bounds__(256) k_prims_partial(const float *__restrict__ t, const float *__restrict__ q,
+                                                       const float *__restrict__ s, int n, int M,
+                                                       Pose *__restrict__ pose, Xform *__restrict__ xf,
+                                                       float4 *__restrict__ pbox, float *__restrict__ partial) {
+  __shared__ float sb[8][6];
+  const int k = blockIdx.x * 256 + threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  if (k < n) {
+    prim_setup(t, q, s, k, M, pose, xf, pbox);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) b[j] = b[3 + j] = t[3 * k + j];
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    b[j] = warp_min(b[j]);
+    b[3 + j] = warp_max(b[3 + j]);
+  }
+  if (lane == 0)
+    for (int j = 0; j < 6; ++j) sb[warp][j] = b[j];
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    float v = sb[0][threadIdx.x];
+    for (int w = 1; w < 8; ++w) v = threadIdx.x < 3 ? fminf(v, sb[w][threadIdx.x]) : fmaxf(v, sb[w][threadIdx.x]);
+    partial[6 * blockIdx.x + threadIdx.x] = v;
+  }
 }
 
 // ------------------------------------------------------------------ 3. radix sort
@@ -226,76 +270,367 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const uint32_t *_
   }
 }
 
-// ------------------------------------------------------------------ 4. hierarchy
-__device__ __forceinline__ int delta(const uint32_t *__restrict__ km, const int *__restrict__ kv, int n, int i,
-                                     int j) {
-  if (j < 0 || j >= n) return -1;
-  uint64_t a = ((uint64_t)km[i] << 32) | (uint32_t)kv[i];
-  uint64_t b = ((uint64_t)km[j] << 32) | (uint32_t)kv[j];
-  return __clzll(a ^ b);
+// One-block sort for mid-sized n: reduces the per-block centre bounds, computes the
+// Morton codes and sorts (code, primitive index) pairs: by buckets of the top code
+// bits and an insertion sort per bucket, or, if some bucket is large (clustered
+// centres), by a stable LSD radix (3 passes of 10 bits, ping-pong in global memory,
+// tiles of 1024 keys in order). One launch instead of the multi-block sort's twelve;
+// the result lands in (ka, va).
+constexpr int SORT1_THREADS = 1024;
+constexpr int SORT1_BITS = 10, SORT1_BINS = 1 << SORT1_BITS;
+constexpr size_t SORT1_SMEM = sizeof(int) * (size_t)(SORT1_THREADS / 32) * SORT1_BINS;
+constexpr int SORT1_BUCKET_BITS = 13, SORT1_BUCKETS = 1 << SORT1_BUCKET_BITS;
+constexpr int SORT1_BUCKET_MAX = 64;  // largest bucket the insertion sort takes
+static_assert(2 * SORT1_BUCKETS * sizeof(int) <= SORT1_SMEM, "bucket arrays live in the digit-count area");
+static_assert(SORT1_BUCKETS % SORT1_THREADS == 0, "whole buckets per thread");
+
+__global__ void __launch_bounds__(SORT1_THREADS) k_sort_one(const float *__restrict__ t, int n,
+                                                            const float *__restrict__ partial, int n_partial,
+                                                            float *__restrict__ scene_out, uint32_t *ka, int *va,
+                                                            uint32_t *kb, int *vb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int(*wcnt)[SORT1_BINS] = reinterpret_cast<int(*)[SORT1_BINS]>(smem_raw);  // [32][1024] per-warp digit counts
+  __shared__ int base[SORT1_BINS + 1];
+  __shared__ int tile_total[SORT1_BINS];
+  __shared__ float sscene[6];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  // centre bounds from the partials, then the codes (into kb/vb: the odd pass count
+  // ends in ka/va)
+  if (warp == 0 && lane < 6) {
+    float v = lane < 3 ? INFINITY : -INFINITY;
+    for (int b = 0; b < n_partial; ++b) v = lane < 3 ? fminf(v, partial[6 * b + lane]) : fmaxf(v, partial[6 * b + lane]);
+    sscene[lane] = v;
+    scene_out[lane] = v;
+  }
+  __syncthreads();
+  const float sc[6] = {sscene[0], sscene[1], sscene[2], sscene[3], sscene[4], sscene[5]};
+  for (int k = tid; k < n; k += SORT1_THREADS) {
+    kb[k] = morton_code(t, k, sc);
+    vb[k] = k;
+  }
+  __syncthreads();
+
+  // Usual case: bucket by the top 13 code bits (atomic scatter), then sort each bucket
+  // by (code, index) with insertion. The keys are unique, so this is the radix order.
+  {
+    int *cnt = reinterpret_cast<int *>(smem_raw);  // [8192] counts, then bucket starts
+    int *cur = cnt + SORT1_BUCKETS;                // [8192] scatter cursors
+    for (int b = tid; b < SORT1_BUCKETS; b += SORT1_THREADS) cnt[b] = 0;
+    __syncthreads();
+    for (int k = tid; k < n; k += SORT1_THREADS) atomicAdd(&cnt[kb[k] >> (30 - SORT1_BUCKET_BITS)], 1);
+    __syncthreads();
+    // largest bucket, and this thread's 8 consecutive buckets' total
+    constexpr int PER = SORT1_BUCKETS / SORT1_THREADS;
+    int mx = 0, own = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int c = cnt[PER * tid + j];
+      mx = max(mx, c);
+      own += c;
+    }
+    mx = __reduce_max_sync(FULL, mx);
+    int incl = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) {
+      tile_total[warp] = incl;
+      base[warp] = mx;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const int w = tile_total[lane];
+      int iw = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(FULL, iw, o);
+        if (lane >= o) iw += u;
+      }
+      tile_total[lane] = iw - w;
+      const int m = __reduce_max_sync(FULL, base[lane]);
+      if (lane == 0) base[32] = m;
+    }
+    __syncthreads();
+    const int bmax = base[32];
+    if (bmax <= SORT1_BUCKET_MAX) {
+      int run = tile_total[warp] + incl - own;
+#pragma unroll
+      for (int j = 0; j < PER; ++j) {
+        const int c = cnt[PER * tid + j];
+        cnt[PER * tid + j] = run;
+        cur[PER * tid + j] = run;
+        run += c;
+      }
+      __syncthreads();
+      for (int k = tid; k < n; k += SORT1_THREADS) {
+        const uint32_t key = kb[k];
+        const int pos = atomicAdd(&cur[key >> (30 - SORT1_BUCKET_BITS)], 1);
+        ka[pos] = key;
+        va[pos] = k;
+      }
+      __syncthreads();
+      for (int b = tid; b < SORT1_BUCKETS; b += SORT1_THREADS) {
+        const int s0 = cnt[b], e0 = b + 1 < SORT1_BUCKETS ? cnt[b + 1] : n;
+        for (int x = s0 + 1; x < e0; ++x) {
+          const uint32_t kx = ka[x];
+          const int vx = va[x];
+          const uint64_t cx = ((uint64_t)kx << 32) | (uint32_t)vx;
+          int y = x - 1;
+          while (y >= s0 && (((uint64_t)ka[y] << 32) | (uint32_t)va[y]) > cx) {
+            ka[y + 1] = ka[y];
+            va[y + 1] = va[y];
+            --y;
+          }
+          ka[y + 1] = kx;
+          va[y + 1] = vx;
+        }
+      }
+      return;
+    }
+    __syncthreads();  // a bucket holds more than SORT1_BUCKET_MAX keys: stable radix below
+  }
+
+  const uint32_t *kin = kb;
+  const int *vin = vb;
+  uint32_t *kout = ka;
+  int *vout = va;
+  for (int pass = 0; pass < 3; ++pass) {
+    const int shift = SORT1_BITS * pass;
+    // digit histogram and its exclusive scan
+    base[tid] = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += SORT1_THREADS) atomicAdd(&base[(kin[i] >> shift) & (SORT1_BINS - 1)], 1);
+    __syncthreads();
+    {
+      const int v = base[tid];
+      int incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += u;
+      }
+      if (lane == 31) tile_total[warp] = incl;  // per-warp sums (reused below)
+      __syncthreads();
+      if (warp == 0) {
+        const int w = tile_total[lane];
+        int iw = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int u = __shfl_up_sync(FULL, iw, o);
+          if (lane >= o) iw += u;
+        }
+        tile_total[lane] = iw - w;
+      }
+      __syncthreads();
+      base[tid] = tile_total[warp] + incl - v;
+      __syncthreads();
+    }
+    // stable scatter, one tile of 1024 keys at a time, in order
+    for (int t0 = 0; t0 < n; t0 += SORT1_THREADS) {
+      const int i = t0 + tid;
+      const bool valid = i < n;
+      const uint32_t key = valid ? kin[i] : 0u;
+      const int val = valid ? vin[i] : 0;
+      const int d = valid ? (int)((key >> shift) & (SORT1_BINS - 1)) : SORT1_BINS + lane;
+#pragma unroll 4
+      for (int w = 0; w < 32; ++w) wcnt[w][tid] = 0;
+      __syncthreads();
+      const unsigned peers = __match_any_sync(FULL, d);
+      const int rank = __popc(peers & lt);
+      if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+      __syncthreads();
+      int sum = 0;
+      for (int w = 0; w < 32; ++w) {
+        const int c = wcnt[w][tid];
+        wcnt[w][tid] = sum;
+        sum += c;
+      }
+      tile_total[tid] = sum;
+      __syncthreads();
+      if (valid) {
+        const int pos = base[d] + wcnt[warp][d] + rank;
+        kout[pos] = key;
+        vout[pos] = val;
+      }
+      __syncthreads();
+      base[tid] += tile_total[tid];
+      __syncthreads();
+    }
+    // every block thread wrote its keys; make them visible to the next pass's reads
+    __threadfence_block();
+    const uint32_t *tk = kout;
+    const int *tv = vout;
+    kout = const_cast<uint32_t *>(kin);
+    vout = const_cast<int *>(vin);
+    kin = tk;
+    vin = tv;
+  }
 }
 
-__global__ void k_hierarchy(const uint32_t *__restrict__ km, const int *__restrict__ kv, int n,
-                            const float4 *__restrict__ pbox, Node *__restrict__ nodes, int *__restrict__ parent) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  // leaf i: node n-1+i
-  {
-    int k = kv[i];
-    float4 lo = pbox[2 * k], hi = pbox[2 * k + 1];
-    Node L;
-    L.lox = lo.x; L.loy = lo.y; L.loz = lo.z; L.left = -1 - k;
-    L.hix = hi.x; L.hiy = hi.y; L.hiz = hi.z; L.right = 0;
-    nodes[n - 1 + i] = L;
-  }
-  if (i == 0) parent[0] = -1;
-  if (i >= n - 1) return;
-  // internal node i: direction of its range, its other end j, and the split
-  int d = (delta(km, kv, n, i, i + 1) - delta(km, kv, n, i, i - 1)) >= 0 ? 1 : -1;
-  int dmin = delta(km, kv, n, i, i - d);
+// ------------------------------------------------------------------ 4. hierarchy
+// Children of internal node i of the binary radix tree over n sorted unique 64-bit
+// keys (key(i) = morton << 32 | primitive): the direction of its range, its other
+// end j, and the split (Karras). Children >= n-1 are leaves (n-1 + sorted index).
+template <class Key>
+__device__ __forceinline__ void internal_children(const Key &key, int n, int i, int &lc, int &rc, int &j_end) {
+  auto delta = [&](int a, int b) -> int {
+    if (b < 0 || b >= n) return -1;
+    return __clzll(key(a) ^ key(b));
+  };
+  int d = (delta(i, i + 1) - delta(i, i - 1)) >= 0 ? 1 : -1;
+  int dmin = delta(i, i - d);
   int lmax = 2;
-  while (delta(km, kv, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  while (delta(i, i + lmax * d) > dmin) lmax <<= 1;
   int l = 0;
   for (int step = lmax >> 1; step >= 1; step >>= 1)
-    if (delta(km, kv, n, i, i + (l + step) * d) > dmin) l += step;
+    if (delta(i, i + (l + step) * d) > dmin) l += step;
   int j = i + l * d;
-  int dnode = delta(km, kv, n, i, j);
+  int dnode = delta(i, j);
   int sgap = 0;
   for (int div = 2;; div <<= 1) {
     int step = (l + div - 1) / div;
-    if (delta(km, kv, n, i, i + (sgap + step) * d) > dnode) sgap += step;
+    if (delta(i, i + (sgap + step) * d) > dnode) sgap += step;
     if (step == 1) break;
   }
   int g = i + sgap * d + min(d, 0);
-  int lc = (min(i, j) == g) ? (n - 1 + g) : g;
-  int rc = (max(i, j) == g + 1) ? (n - 1 + g + 1) : g + 1;
+  lc = (min(i, j) == g) ? (n - 1 + g) : g;
+  rc = (max(i, j) == g + 1) ? (n - 1 + g + 1) : g + 1;
+  j_end = j;
+}
+
+__device__ __forceinline__ void write_leaf(Node *__restrict__ nodes, int n, int i, int k,
+                                           const float4 *__restrict__ pbox) {
+  float4 lo = pbox[2 * k], hi = pbox[2 * k + 1];
+  Node L;
+  L.lox = lo.x; L.loy = lo.y; L.loz = lo.z; L.left = -1 - k;
+  L.hix = hi.x; L.hiy = hi.y; L.hiz = hi.z; L.right = 0;
+  nodes[n - 1 + i] = L;
+}
+
+__device__ __forceinline__ void write_internal(Node *__restrict__ nodes, int i, int lc, int rc) {
   Node N;
   N.lox = N.loy = N.loz = 0.0f;
   N.hix = N.hiy = N.hiz = 0.0f;
   N.left = lc;
   N.right = rc;
   nodes[i] = N;
-  parent[lc] = i;
-  parent[rc] = i;
+}
+
+// One thread per node: leaf i (node n-1+i) and internal node i with the sorted leaf
+// range [first, last] it covers (range[i]). Blocks of 1024 also union their leaves'
+// boxes in chunks of 32 (chunk1, one per warp) and 1024 (chunk2, one per block) for
+// the range refit.
+constexpr int HIER_THREADS = 1024;
+__global__ void __launch_bounds__(HIER_THREADS) k_hierarchy(const uint32_t *__restrict__ km,
+                                                            const int *__restrict__ kv, int n,
+                                                            const float4 *__restrict__ pbox, Node *__restrict__ nodes,
+                                                            int2 *__restrict__ range, float4 *__restrict__ chunk1,
+                                                            float4 *__restrict__ chunk2) {
+  __shared__ float sc[32][6];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int i = blockIdx.x * HIER_THREADS + tid;
+  float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  if (i < n) {
+    const int k = kv[i];
+    write_leaf(nodes, n, i, k, pbox);  // leaf i: node n-1+i
+    const float4 lo = pbox[2 * k], hi = pbox[2 * k + 1];
+    b[0] = lo.x; b[1] = lo.y; b[2] = lo.z; b[3] = hi.x; b[4] = hi.y; b[5] = hi.z;
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    b[j] = warp_min(b[j]);
+    b[3 + j] = warp_max(b[3 + j]);
+  }
+  if (lane == 0) {
+    if (i < n) {
+      chunk1[2 * (i >> 5)] = make_float4(b[0], b[1], b[2], 0.0f);
+      chunk1[2 * (i >> 5) + 1] = make_float4(b[3], b[4], b[5], 0.0f);
+    }
+#pragma unroll
+    for (int j = 0; j < 6; ++j) sc[warp][j] = b[j];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    float c[6];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      c[j] = warp_min(sc[lane][j]);
+      c[3 + j] = warp_max(sc[lane][3 + j]);
+    }
+    if (lane == 0) {
+      chunk2[2 * blockIdx.x] = make_float4(c[0], c[1], c[2], 0.0f);
+      chunk2[2 * blockIdx.x + 1] = make_float4(c[3], c[4], c[5], 0.0f);
+    }
+  }
+  if (i >= n - 1) return;
+  auto key = [&](int a) -> uint64_t { return ((uint64_t)km[a] << 32) | (uint32_t)kv[a]; };
+  int lc, rc, j;
+  internal_children(key, n, i, lc, rc, j);
+  write_internal(nodes, i, lc, rc);
+  range[i] = make_int2(min(i, j), max(i, j));
 }
 
 // ------------------------------------------------------------------ 5. refit
-__global__ void k_refit(Node *nodes, const int *__restrict__ parent, int *flags, int n) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int node = parent[n - 1 + i];
-  while (node >= 0) {
-    __threadfence();
-    if (atomicAdd(&flags[node], 1) == 0) return;  // the sibling subtree is not done yet
-    __threadfence();
-    int l = __ldcg(&nodes[node].left), r = __ldcg(&nodes[node].right);
-    const float4 *L = reinterpret_cast<const float4 *>(&nodes[l]);
-    const float4 *Rr = reinterpret_cast<const float4 *>(&nodes[r]);
-    float4 a0 = __ldcg(L), a1 = __ldcg(L + 1), b0 = __ldcg(Rr), b1 = __ldcg(Rr + 1);
-    float4 *D = reinterpret_cast<float4 *>(&nodes[node]);
-    __stcg(D, make_float4(fminf(a0.x, b0.x), fminf(a0.y, b0.y), fminf(a0.z, b0.z), __int_as_float(l)));
-    __stcg(D + 1, make_float4(fmaxf(a1.x, b1.x), fmaxf(a1.y, b1.y), fmaxf(a1.z, b1.z), __int_as_float(r)));
-    node = parent[node];
+// Box of every internal node as the union of the leaves in its sorted range (the
+// same min/max as a bottom-up union of children, so the same bits): one warp per
+// node covers the range with whole 1024-leaf and 32-leaf chunks where it can and
+// single leaves at its ends, a few coalesced loads per lane. No node waits for
+// another.
+constexpr int REFIT_WARPS = 8;
+__global__ void __launch_bounds__(REFIT_WARPS * 32) k_refit_ranges(Node *__restrict__ nodes,
+                                                                   const int2 *__restrict__ range,
+                                                                   const float4 *__restrict__ chunk1,
+                                                                   const float4 *__restrict__ chunk2, int n) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * REFIT_WARPS + (threadIdx.x >> 5);
+  if (i >= n - 1) return;
+  const int2 r = range[i];
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  // union of boxes [s, e) of an array of {lo, hi} float4 pairs
+  auto add = [&](const float4 *box, int s, int e) {
+    for (int a = s + lane; a < e; a += 32) {
+      const float4 b0 = __ldg(box + 2 * a), b1 = __ldg(box + 2 * a + 1);
+      lo[0] = fminf(lo[0], b0.x);
+      lo[1] = fminf(lo[1], b0.y);
+      lo[2] = fminf(lo[2], b0.z);
+      hi[0] = fmaxf(hi[0], b1.x);
+      hi[1] = fmaxf(hi[1], b1.y);
+      hi[2] = fmaxf(hi[2], b1.z);
+    }
+  };
+  const float4 *leaf = reinterpret_cast<const float4 *>(nodes + (n - 1));
+  const int a = r.x, e = r.y + 1;
+  if (e - a <= 64) {
+    add(leaf, a, e);
+  } else {
+    const int ca = (a + 31) >> 5, cb = e >> 5;  // whole 32-leaf chunks [ca, cb)
+    add(leaf, a, ca * 32);
+    add(leaf, cb * 32, e);
+    if (cb - ca <= 64) {
+      add(chunk1, ca, cb);
+    } else {
+      const int da = (ca + 31) >> 5, db = cb >> 5;  // whole 1024-leaf chunks [da, db)
+      add(chunk1, ca, da * 32);
+      add(chunk1, db * 32, cb);
+      add(chunk2, da, db);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    lo[j] = warp_min(lo[j]);
+    hi[j] = warp_max(hi[j]);
+  }
+  if (lane == 0) {
+    Node &N = nodes[i];
+    N.lox = lo[0];
+    N.loy = lo[1];
+    N.loz = lo[2];
+    N.hix = hi[0];
+    N.hiy = hi[1];
+    N.hiz = hi[2];
   }
 }
 
@@ -323,7 +658,6 @@ cudaError_t bvh_reserve(BvhBuffers &b, int n) {
   size_t o_cnt = off; off = align_up(off + (size_t)256 * G * sizeof(int));
   size_t o_nodes = off; off = align_up(off + (size_t)(2 * cap) * sizeof(Node));
   size_t o_par = off; off = align_up(off + (size_t)(2 * cap) * sizeof(int));
-  size_t o_flags = off; off = align_up(off + (size_t)cap * sizeof(int));
   size_t o_gmc = off; off = align_up(off + (size_t)cap * 12 * sizeof(float));
   char *p = nullptr;
   cudaError_t e = cudaMalloc(&p, off);
@@ -342,7 +676,6 @@ cudaError_t bvh_reserve(BvhBuffers &b, int n) {
   b.counts = reinterpret_cast<int *>(p + o_cnt);
   b.nodes = reinterpret_cast<Node *>(p + o_nodes);
   b.parent = reinterpret_cast<int *>(p + o_par);
-  b.flags = reinterpret_cast<int *>(p + o_flags);
   b.gmc = reinterpret_cast<float *>(p + o_gmc);
   return cudaSuccess;
 }
@@ -357,25 +690,44 @@ cudaError_t bvh_build(BvhBuffers &b, const float *t, const float *q, const float
   b.n = n;
   b.M = M;
   if (n == 0) return cudaGetLastError();
-  k_bounds<<<1, 1024, 0, st>>>(t, n, b.scene);
-  k_prims<<<(n + 255) / 256, 256, 0, st>>>(t, q, s, n, M, b.scene, b.pose, b.xf, b.pbox, b.keys_a, b.vals_a);
-  int G = (n + SORT_TILE - 1) / SORT_TILE;
-  uint32_t *kin = b.keys_a, *kout = b.keys_b;
-  int *vin = b.vals_a, *vout = b.vals_b;
-  for (int pass = 0; pass < 4; ++pass) {
-    int shift = 8 * pass;
-    k_sort_count<<<G, SORT_THREADS, 0, st>>>(kin, n, shift, G, b.counts);
-    k_scan_excl<<<1, 1024, 0, st>>>(b.counts, 256 * G);
-    k_sort_scatter<<<G, SORT_THREADS, 0, st>>>(kin, vin, n, shift, G, b.counts, kout, vout);
-    uint32_t *tk = kin; kin = kout; kout = tk;
-    int *tv = vin; vin = vout; vout = tv;
+  const int G = (n + SORT_TILE - 1) / SORT_TILE;
+  const int n_partial = (n + 255) / 256;
+  if (n <= BVH_SORT1_N && (size_t)6 * n_partial <= (size_t)256 * G) {
+    // mid-sized n: primitives with per-block bounds, then one block sorts
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(k_sort_one, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SORT1_SMEM);
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+    float *partial = reinterpret_cast<float *>(b.counts);  // 6 floats per 256 primitives
+    k_prims_partial<<<n_partial, 256, 0, st>>>(t, q, s, n, M, b.pose, b.xf, b.pbox, partial);
+    k_sort_one<<<1, SORT1_THREADS, SORT1_SMEM, st>>>(t, n, partial, n_partial, b.scene, b.keys_a, b.vals_a,
+                                                     b.keys_b, b.vals_b);
+  } else {
+    k_bounds<<<1, 1024, 0, st>>>(t, n, b.scene);
+    k_prims<<<(n + 255) / 256, 256, 0, st>>>(t, q, s, n, M, b.scene, b.pose, b.xf, b.pbox, b.keys_a, b.vals_a);
+    uint32_t *kin = b.keys_a, *kout = b.keys_b;
+    int *vin = b.vals_a, *vout = b.vals_b;
+    for (int pass = 0; pass < 4; ++pass) {
+      int shift = 8 * pass;
+      k_sort_count<<<G, SORT_THREADS, 0, st>>>(kin, n, shift, G, b.counts);
+      k_scan_excl<<<1, 1024, 0, st>>>(b.counts, 256 * G);
+      k_sort_scatter<<<G, SORT_THREADS, 0, st>>>(kin, vin, n, shift, G, b.counts, kout, vout);
+      uint32_t *tk = kin; kin = kout; kout = tk;
+      int *tv = vin; vin = vout; vout = tv;
+    }
+    // four passes: the sorted data is back in keys_a / vals_a
   }
-  // four passes: the sorted data is back in keys_a / vals_a
-  k_hierarchy<<<(n + 255) / 256, 256, 0, st>>>(b.keys_a, b.vals_a, n, b.pbox, b.nodes, b.parent);
-  if (n > 1) {
-    cudaMemsetAsync(b.flags, 0, sizeof(int) * (size_t)(n - 1), st);
-    k_refit<<<(n + 255) / 256, 256, 0, st>>>(b.nodes, b.parent, b.flags, n);
-  }
+  // scratch after the sort: ranges in the parent buffer (2n ints), chunk boxes in the
+  // second key and value buffers (n/32 and n/1024 boxes of 32 bytes fit in 4n bytes)
+  int2 *range = reinterpret_cast<int2 *>(b.parent);
+  float4 *chunk1 = reinterpret_cast<float4 *>(b.keys_b), *chunk2 = reinterpret_cast<float4 *>(b.vals_b);
+  k_hierarchy<<<(n + HIER_THREADS - 1) / HIER_THREADS, HIER_THREADS, 0, st>>>(b.keys_a, b.vals_a, n, b.pbox, b.nodes,
+                                                                              range, chunk1, chunk2);
+  if (n > 1)
+    k_refit_ranges<<<(n - 1 + REFIT_WARPS - 1) / REFIT_WARPS, REFIT_WARPS * 32, 0, st>>>(b.nodes, range, chunk1,
+                                                                                          chunk2, n);
   return cudaGetLastError();
 }
 

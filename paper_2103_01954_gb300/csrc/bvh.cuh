@@ -6,6 +6,7 @@
 namespace mvp {
 
 constexpr int BVH_SORT_TILE = 2048;  // keys per radix-sort block (sizes BvhBuffers::counts)
+constexpr int BVH_SORT1_N = 8192;    // primitives up to which one block sorts the keys
 
 struct BvhBuffers {
   char *base = nullptr;
@@ -21,8 +22,7 @@ struct BvhBuffers {
   int *vals_a = nullptr, *vals_b = nullptr;       // primitive ids (sorted result in vals_a)
   int *counts = nullptr;   // radix digit counts [256][blocks]
   Node *nodes = nullptr;   // [2n-1]
-  int *parent = nullptr;   // [2n-1]
-  int *flags = nullptr;    // [n-1] refit arrival counters
+  int *parent = nullptr;   // [2n]: the internal nodes' sorted leaf ranges (int2) during the build
   float *gmc = nullptr;    // [n][12] adjoint accumulators of the march transform
 };
 

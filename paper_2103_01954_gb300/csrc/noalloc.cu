@@ -42,8 +42,7 @@ constexpr size_t kOffValsB = align256(kOffValsA + (size_t)kMaxPrims * sizeof(int
 constexpr size_t kOffCounts = align256(kOffValsB + (size_t)kMaxPrims * sizeof(int));
 constexpr size_t kOffNodes = align256(kOffCounts + (size_t)256 * kMaxSortBlocks * sizeof(int));
 constexpr size_t kOffParent = align256(kOffNodes + (size_t)2 * kMaxPrims * sizeof(mvp::Node));
-constexpr size_t kOffFlags = align256(kOffParent + (size_t)2 * kMaxPrims * sizeof(int));
-constexpr size_t kBytes = align256(kOffFlags + (size_t)kMaxPrims * sizeof(int));
+constexpr size_t kBytes = align256(kOffParent + (size_t)2 * kMaxPrims * sizeof(int));
 
 static __device__ __align__(256) unsigned char g_static_scratch[kBytes];
 
@@ -113,7 +112,6 @@ extern "C" mvp_status mvp_raymarch_fwd_static(const mvp_prims *prims, const mvp_
   b.counts = reinterpret_cast<int *>(base + kOffCounts);
   b.nodes = reinterpret_cast<mvp::Node *>(base + kOffNodes);
   b.parent = reinterpret_cast<int *>(base + kOffParent);
-  b.flags = reinterpret_cast<int *>(base + kOffFlags);
   cudaError_t e = mvp::bvh_build(b, prims->t, prims->q, prims->s, prims->n, prims->M, st);
   if (e != cudaSuccess) return reject(MVP_ERR_CUDA, "BVH build launch failed");
 

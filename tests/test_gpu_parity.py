@@ -41,13 +41,15 @@ def _scene_n(n, seed=0, dup=False):
         sc = synthetic.make_scene(1, 4, seed)
         return synthetic.Scene(t=sc.t[:0], q=sc.q[:0], s=sc.s[:0], payload=sc.payload[:0], M=4)
     sc = synthetic.make_scene(n, 4, seed, layout="shell", s_range=(0.02, 0.05), empty_frac=0.5)
-    if dup and n > 20:
+    if dup == "cluster":  # 200 equal centres: one Morton code for all of them
+        sc.t[:200] = sc.t[0]
+    elif dup and n > 20:
         sc.t[10:20] = sc.t[3]
     return sc
 
 
-@pytest.mark.parametrize("n,dup", [(1, False), (2, False), (3, False), (50, True), (513, False), (5000, True),
-                                   (40000, False)])
+@pytest.mark.parametrize("n,dup", [(1, False), (2, False), (3, False), (50, True), (513, False), (1000, "cluster"),
+                                   (4096, "cluster"), (5000, True), (8192, True), (8193, False), (40000, False)])
 def test_bvh_keys_and_tree_bit_exact(n, dup):
     sc = _scene_n(n, dup=dup)
     rays = rays_from([0, 0, 3], [0, 0, -1], 1.0, 5.0, 0.01)
