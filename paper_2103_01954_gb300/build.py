@@ -78,6 +78,13 @@ def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
     os.replace(tmp, out)
     for o in objs:
         os.remove(o)
+    # libraries of earlier sources are stale (a process that loaded one keeps its mapping)
+    for old in glob.glob(os.path.join(BUILD, "libmvp_*.so")):
+        if old != out:
+            try:
+                os.remove(old)
+            except OSError:
+                pass
     return out
 
 
