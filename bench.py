@@ -255,22 +255,21 @@ def _cpu_baseline(seconds: float = 15.0):
                       f"pruned mode, {cores} OpenMP threads, {total_s:.1f} s"}
 
 
-def _traffic(kernel_key: str):
-    """DRAM bytes per launch of the march kernel from the committed ncu summary, if it
-    was taken with the current library build."""
+def _ncu_record(kernel_key: str) -> dict:
+    """The committed ncu figures of a kernel (profiles/traffic.json), if they were taken
+    with the kernel's current sources (the digest of the files the record lists), else {}."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
-        return None
+        return {}
     try:
         from paper_2103_01954_gb300 import build as b
 
-        d = json.load(open(p))
-        e = d.get(kernel_key)
-        if e and e.get("source_digest") == b._digest():
-            return e.get("dram_bytes_per_launch")
+        e = json.load(open(p)).get(kernel_key)
+        if e and e.get("source_digest") == b.sources_digest(e["sources"]):
+            return e
     except Exception:
-        return None
-    return None
+        return {}
+    return {}
 
 
 def _serve_trace(T, srv, ids, reqs, arrivals):
@@ -460,9 +459,11 @@ def run_gpu(args):
 
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s (FMA = 2)
+    ncu = _ncu_record("k_march_f32")
     achieved = FLOP_PER_EVAL * n_eval / (march_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / fp32_peak, 4), "traffic": _traffic("k_march_f32"),
+                "frac": round(achieved / fp32_peak, 4), "traffic": ncu.get("dram_bytes_per_launch"),
+                "l1_wavefront_frac": ncu.get("l1_wavefront_frac"),
                 "kernel": "k_march<f32>", "march_ms": round(march_ms, 4), "evaluations": n_eval,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
                 "gather_GBps": round(GATHER_BYTES["f32"] * n_eval / (march_ms * 1e-3) / 1e9, 1),

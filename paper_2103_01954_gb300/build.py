@@ -46,6 +46,19 @@ def _digest() -> str:
     return h.hexdigest()[:16]
 
 
+def sources_digest(names: list[str]) -> str:
+    """Digest of some of the library's sources (file names relative to csrc/, or the
+    header's name) with the compile flags: identifies the build of one kernel."""
+    h = hashlib.sha1()
+    for name in names:
+        f = HEADER if name == os.path.basename(HEADER) else os.path.join(CSRC, name)
+        h.update(name.encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    return h.hexdigest()[:16]
+
+
 def library_path() -> str:
     return os.path.join(BUILD, f"libmvp_{_digest()}.so")
 
