@@ -190,42 +190,89 @@ def _time_steps(torch, step, steps, warmup, flush, time_march=False):
     return [a.elapsed_time(b) for a, b in durs]
 
 
-def _e2e(torch, T, info, steps, warmup):
-    """Same frame through the C ABI from pinned host buffers: copy the frame's inputs
-    (poses, payload, rays) host->device, build + march, read the image back."""
+def _e2e(torch, T, info, steps, warmup, payload_dtype="f32"):
+    """The same frame through the C ABI from pinned host buffers: every step copies its
+    inputs (poses, payload, rays) host->device, builds the BVH, marches, and reads the
+    image back to pinned host memory. Frames are pipelined as a streaming renderer
+    would run them: frame k+1's inputs are copied on a copy stream (into the other of
+    two device buffer sets) while frame k renders, and each image is read back on a
+    third stream. The serial time (one stream, nothing overlapped) is reported beside."""
     scene, rays = info["host"]
     dev = torch.device("cuda", torch.cuda.current_device())
     hs = [torch.from_numpy(a).pin_memory() for a in (scene.t, scene.q, scene.s, scene.payload, rays.o, rays.d)]
-    ds = [torch.empty(h.shape, dtype=h.dtype, device=dev) for h in hs]
-    hout = torch.empty((rays.n, 4), dtype=torch.float32).pin_memory()
+    if payload_dtype != "f32":
+        # the host holds the payload in the reduced type (packed once by mvp_pack_payload)
+        tdt = {"bf16": torch.bfloat16, "f16": torch.float16}[payload_dtype]
+        hs[3] = T.pack_payload(info["ctx"], hs[3].to(dev), tdt).cpu().pin_memory()
+    sets = []
+    for _ in range(2):
+        ds = [torch.empty(h.shape, dtype=h.dtype, device=dev) for h in hs]
+        prims = T.prims_struct(ds[0], ds[1], ds[2], ds[3])
+        rs = T.rays_struct(ds[4], ds[5], t_near=rays.t_near, t_far=rays.t_far, dt=rays.dt, width=rays.width,
+                           height=rays.height)
+        out = torch.empty((rays.n, 4), dtype=torch.float32, device=dev)
+        hout = torch.empty((rays.n, 4), dtype=torch.float32).pin_memory()
+        sets.append({"ds": ds, "prims": prims, "rs": rs, "out": out, "hout": hout,
+                     "copied": torch.cuda.Event(), "rendered": torch.cuda.Event(), "read": torch.cuda.Event()})
     ctx, bvh = info["ctx"], info["bvh"]
-    prims = T.prims_struct(ds[0], ds[1], ds[2], ds[3])
-    rs = T.rays_struct(ds[4], ds[5], t_near=rays.t_near, t_far=rays.t_far, dt=rays.dt, width=rays.width,
-                       height=rays.height)
-    out = info["out"]
+    comp = torch.cuda.current_stream()
+    copy_s, read_s = torch.cuda.Stream(), torch.cuda.Stream()
+    for st in sets:  # both sets start free
+        st["rendered"].record(comp)
+        st["read"].record(comp)
 
-    def step():
-        for h, d in zip(hs, ds):
+    def step(k):
+        st = sets[k % 2]
+        with torch.cuda.stream(copy_s):
+            copy_s.wait_event(st["rendered"])  # the set's previous frame no longer reads its inputs
+            for h, d in zip(hs, st["ds"]):
+                d.copy_(h, non_blocking=True)
+            st["copied"].record(copy_s)
+        comp.wait_event(st["copied"])
+        comp.wait_event(st["read"])  # the set's previous image has been read back
+        bvh.build(st["prims"])
+        T.raymarch_fwd(ctx, st["prims"], bvh, st["rs"], out=st["out"])
+        st["rendered"].record(comp)
+        with torch.cuda.stream(read_s):
+            read_s.wait_event(st["rendered"])
+            st["hout"].copy_(st["out"], non_blocking=True)
+            st["read"].record(read_s)
+
+    def serial_step():
+        st = sets[0]
+        for h, d in zip(hs, st["ds"]):
             d.copy_(h, non_blocking=True)
-        bvh.build(prims)
-        T.raymarch_fwd(ctx, prims, bvh, rs, out=out)
-        hout.copy_(out, non_blocking=True)
+        bvh.build(st["prims"])
+        T.raymarch_fwd(ctx, st["prims"], bvh, st["rs"], out=st["out"])
+        st["hout"].copy_(st["out"], non_blocking=True)
 
+    def timed(fn, n):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(comp)
+        for k in range(n):
+            fn(k)
+        comp.wait_stream(copy_s)
+        comp.wait_stream(read_s)
+        e1.record(comp)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    for k in range(warmup):
+        step(k)
+    ms = timed(step, steps)
     for _ in range(warmup):
-        step()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        step()
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
+        serial_step()
+    ms_serial = timed(lambda k: serial_step(), steps)
+    ctx.sync()
     h2d = sum(h.numel() * h.element_size() for h in hs)
-    d2h = hout.numel() * hout.element_size()
+    d2h = rays.n * 4 * 4
     return {"value": rays.n / (ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": ms, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h}
+            "d2h_bytes_per_step": d2h, "serial_ms_per_step": ms_serial,
+            "serial_value": rays.n / (ms_serial * 1e-3) / 1e6,
+            "pipeline": "frame k+1's inputs copied (copy stream, second buffer set) while frame k renders; "
+                        "images read back on a third stream; every copy inside the timed region",
+            "payload_dtype": payload_dtype}
 
 
 def _cpu_baseline(seconds: float = 15.0):
@@ -484,7 +531,7 @@ def run_gpu(args):
 
         dist.barrier()
     if rank == 0 and not args.quick:
-        result["e2e"] = _e2e(torch, T, info, max(3, args.steps // 2), 2)
+        result["e2e"] = _e2e(torch, T, info, max(20, args.steps), 3)
     del info, step
     torch.cuda.empty_cache()
 
@@ -501,6 +548,10 @@ def run_gpu(args):
             mm = float(np.mean([a.elapsed_time(b) for a, b in inf["ev"]["march"]]))
             variants[name] = {"value": round(nr / (m * 1e-3) / 1e6, 3), "unit": "Mrays/s", "ms_per_step": round(m, 4),
                               "march_ms": round(mm, 4), "workload": cfg, "payload_dtype": dtype}
+            if name == "fwd_bf16":
+                # end to end with the payload streamed from the host as BF16 (half the bytes)
+                e = _e2e(torch, T, inf, max(20, args.steps), 3, payload_dtype="bf16")
+                variants["e2e_bf16"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in e.items()}
             del st, inf
             torch.cuda.empty_cache()
         st, nr, inf = _frame_runner("diff_512x32^3_4x512x512", 0, "f32", True, torch, T, synthetic)
@@ -514,6 +565,8 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         if variants.get("fwd_bf16"):
             variants["bf16_over_f32"] = round(variants["fwd_bf16"]["value"] / value, 3)
+        if variants.get("e2e_bf16") and result.get("e2e"):
+            variants["e2e_bf16_over_f32"] = round(variants["e2e_bf16"]["value"] / result["e2e"]["value"], 3)
         result["variants"] = variants
         if args.serving_requests > 0:
             rates = [float(r) for r in args.serving_rates.split(",")]
