@@ -86,9 +86,9 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
       const uint32_t rg = sh.erng[e][lane];
       const int lo = (int)(rg & 0xffffu), hi = (int)(rg >> 16);
       const float4 tk = __ldg(reinterpret_cast<const float4 *>(a.pose + k) + 2);  // {R22, t0, t1, t2}
-      float acc[12];
+      float2 acc[6];  // the 12 pose accumulators as packed pairs
 #pragma unroll
-      for (int c = 0; c < 12; ++c) acc[c] = 0.0f;
+      for (int c = 0; c < 6; ++c) acc[c] = make_float2(0.0f, 0.0f);
       // Each lane walks its own samples of the primitive from its own first one (the
       // samples are independent here), so the warp loops max(count) times rather
       // than over the union of the lanes' ranges.
@@ -145,31 +145,24 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
           gv = make_float4(a.dt * val.w * gr, a.dt * val.w * gg, a.dt * val.w * gb,
                            a.dt * (ga + gr * val.x + gg * val.y + gb * val.z));
           if (b.gmc) {
-            // dval/du along each axis (zero along an axis where u was clamped)
-            const float4 dx0 = lerp4(make_float4(c001.x - c000.x, c001.y - c000.y, c001.z - c000.z, c001.w - c000.w),
-                                     make_float4(c011.x - c010.x, c011.y - c010.y, c011.z - c010.z, c011.w - c010.w), fy);
-            const float4 dx1 = lerp4(make_float4(c101.x - c100.x, c101.y - c100.y, c101.z - c100.z, c101.w - c100.w),
-                                     make_float4(c111.x - c110.x, c111.y - c110.y, c111.z - c110.z, c111.w - c110.w), fy);
-            const float4 dvx = lerp4(dx0, dx1, fz);
-            const float4 dvy = lerp4(make_float4(c01.x - c00.x, c01.y - c00.y, c01.z - c00.z, c01.w - c00.w),
-                                     make_float4(c11.x - c10.x, c11.y - c10.y, c11.z - c10.z, c11.w - c10.w), fz);
-            const float4 dvz = make_float4(c1.x - c0.x, c1.y - c0.y, c1.z - c0.z, c1.w - c0.w);
-            const float gux = kx ? gv.x * dvx.x + gv.y * dvx.y + gv.z * dvx.z + gv.w * dvx.w : 0.0f;
-            const float guy = ky ? gv.x * dvy.x + gv.y * dvy.y + gv.z * dvy.z + gv.w * dvy.w : 0.0f;
-            const float guz = kz ? gv.x * dvz.x + gv.y * dvz.y + gv.z * dvz.z + gv.w * dvz.w : 0.0f;
+            // dval/du along each axis (zero along an axis where u was clamped), on packed pairs
+            const float2 wz = splat2(fz), nwz = splat2(-fz);
+            const float4 dx0 = lerp4x2(sub4x2(c001, c000), sub4x2(c011, c010), wy, nwy);
+            const float4 dx1 = lerp4x2(sub4x2(c101, c100), sub4x2(c111, c110), wy, nwy);
+            const float4 dvx = lerp4x2(dx0, dx1, wz, nwz);
+            const float4 dvy = lerp4x2(sub4x2(c01, c00), sub4x2(c11, c10), wz, nwz);
+            const float4 dvz = sub4x2(c1, c0);
+            const float gux = kx ? dot4x2(gv, dvx) : 0.0f;
+            const float guy = ky ? dot4x2(gv, dvy) : 0.0f;
+            const float guz = kz ? dot4x2(gv, dvz) : 0.0f;
             const float p0 = x0 - tk.y, p1 = x1 - tk.z, p2 = x2 - tk.w;
-            acc[0] = fmaf(gux, p0, acc[0]);
-            acc[1] = fmaf(gux, p1, acc[1]);
-            acc[2] = fmaf(gux, p2, acc[2]);
-            acc[3] = fmaf(guy, p0, acc[3]);
-            acc[4] = fmaf(guy, p1, acc[4]);
-            acc[5] = fmaf(guy, p2, acc[5]);
-            acc[6] = fmaf(guz, p0, acc[6]);
-            acc[7] = fmaf(guz, p1, acc[7]);
-            acc[8] = fmaf(guz, p2, acc[8]);
-            acc[9] += gux;
-            acc[10] += guy;
-            acc[11] += guz;
+            // acc = (gux p, guy p, guz p, gux, guy, guz) as 6 packed pairs
+            acc[0] = __ffma2_rn(splat2(gux), make_float2(p0, p1), acc[0]);
+            acc[1] = __ffma2_rn(make_float2(gux, guy), make_float2(p2, p0), acc[1]);
+            acc[2] = __ffma2_rn(splat2(guy), make_float2(p1, p2), acc[2]);
+            acc[3] = __ffma2_rn(splat2(guz), make_float2(p0, p1), acc[3]);
+            acc[4] = __ffma2_rn(make_float2(guz, gux), make_float2(p2, 1.0f), acc[4]);
+            acc[5] = __ffma2_rn(make_float2(guy, guz), make_float2(1.0f, 1.0f), acc[5]);
           }
         }
         if (in && b.g_payload) {
@@ -177,8 +170,12 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
           float4 *G = reinterpret_cast<float4 *>(b.g_payload) + kbase + vo;
           const float wx0 = 1.0f - fx, wy0 = 1.0f - fy, wz0 = 1.0f - fz;
           const float w00 = wy0 * wz0, w01 = fy * wz0, w10 = wy0 * fz, w11 = fy * fz;
-#define MVP_SCATTER(off, WGT) \
-  atomicAdd(G + (off), make_float4((WGT) * gv.x, (WGT) * gv.y, (WGT) * gv.z, (WGT) * gv.w))
+          const float2 glo = lo2(gv), ghi = hi2(gv);
+#define MVP_SCATTER(off, WGT)                                                        \
+  {                                                                                  \
+    const float2 wg = splat2(WGT), l_ = __fmul2_rn(wg, glo), h_ = __fmul2_rn(wg, ghi); \
+    atomicAdd(G + (off), make_float4(l_.x, l_.y, h_.x, h_.y));                       \
+  }
           MVP_SCATTER(0, wx0 * w00);
           MVP_SCATTER(1, fx * w00);
           MVP_SCATTER(M, wx0 * w01);
@@ -191,13 +188,17 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
         }
       }
       if (b.gmc) {
+        float sums[12];
 #pragma unroll
-        for (int c = 0; c < 12; ++c) acc[c] = warp_sum(acc[c]);
+        for (int c = 0; c < 6; ++c) {
+          sums[2 * c] = warp_sum(acc[c].x);
+          sums[2 * c + 1] = warp_sum(acc[c].y);
+        }
         if (lane < 12) {
-          float mine = acc[0];
+          float mine = sums[0];
 #pragma unroll
           for (int c = 1; c < 12; ++c)
-            if (lane == c) mine = acc[c];
+            if (lane == c) mine = sums[c];
           if (mine != 0.0f) atomicAdd(b.gmc + 12 * (int64_t)k + lane, mine);
         }
       }

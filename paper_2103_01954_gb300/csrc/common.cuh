@@ -213,6 +213,19 @@ __device__ __forceinline__ float4 lerp4x2(float4 a, float4 b, float2 w2, float2 
   return make_float4(l.x, l.y, h.x, h.y);
 }
 
+// b - a per component on packed pairs (fma(a, -1, b): the correctly rounded difference).
+__device__ __forceinline__ float4 sub4x2(float4 b, float4 a) {
+  const float2 m = make_float2(-1.0f, -1.0f);
+  const float2 l = __ffma2_rn(lo2(a), m, lo2(b)), h = __ffma2_rn(hi2(a), m, hi2(b));
+  return make_float4(l.x, l.y, h.x, h.y);
+}
+
+// a . b over 4 components on packed pairs.
+__device__ __forceinline__ float dot4x2(float4 a, float4 b) {
+  const float2 t = __ffma2_rn(hi2(a), hi2(b), __fmul2_rn(lo2(a), lo2(b)));
+  return t.x + t.y;
+}
+
 __device__ __forceinline__ float warp_min(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(FULL, v, o));
