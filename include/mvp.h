@@ -19,8 +19,9 @@
  *     comment says they synchronise. A NULL stream is the legacy default stream.
  *   - Every call returns an mvp_status; nothing throws or aborts across the ABI.
  *     Host-side argument checks return MVP_ERR_INVALID_ARG before any launch.
- *     Errors found by a kernel (capacity overflow) are recorded in the context's
- *     device status word and reported by the next mvp_ctx_sync on that context.
+ *     Errors found by a kernel (a traversal stack overflow) are recorded in the
+ *     context's device status word and reported by the next mvp_ctx_sync on that
+ *     context.
  *     mvp_last_error() returns a thread-local message for the last failure.
  *   - All floating-point arithmetic on the device is FP32. Payloads may be stored
  *     as FP32, BF16 or FP16; interpolation and compositing are FP32.
@@ -131,10 +132,11 @@ MVP_API mvp_status mvp_bvh_create(mvp_ctx *ctx, mvp_bvh **out);
 MVP_API void mvp_bvh_destroy(mvp_bvh *bvh);
 /* Rebuild the hierarchy over `prims` (the per-frame rebuild of Sec. 3.2.1):
  * per-primitive rotation, oriented-box world bounds and 30-bit Morton code of the
- * centre within the centres' bounds; a stable radix sort of the codes; the binary
- * radix tree of the sorted keys (morton << 32 | k); bottom-up box refit.
- * Reallocation (first use or larger n) synchronises the stream; a rebuild at the
- * same or smaller n allocates nothing and only enqueues kernels. */
+ * centre within the centres' bounds; the keys (morton << 32 | k) sorted; the binary
+ * radix tree of the sorted keys; each node's box = the union of its leaves' boxes.
+ * Four launches up to 8192 primitives, seventeen above. Reallocation (first use or
+ * larger n) synchronises the stream; a rebuild at the same or smaller n allocates
+ * nothing and only enqueues kernels. */
 MVP_API mvp_status mvp_build_bvh(mvp_ctx *ctx, const mvp_prims *prims, mvp_bvh *bvh, mvp_stream stream);
 /* Number of primitives of the last build. */
 MVP_API int32_t mvp_bvh_size(const mvp_bvh *bvh);
