@@ -304,7 +304,14 @@ def _cpu_baseline(seconds: float = 15.0):
         if dt < seconds / 8:
             n *= 2
     cores = os.cpu_count()
+    # the whole tiny frame (8 primitives of 8^3, 64x64), as a second reference point
+    s0, r0, _ = synthetic.make_config("tiny_8x8^3_64x64", 0)
+    t0 = time.perf_counter()
+    oracle.render(s0, r0)
+    tiny_s = time.perf_counter() - t0
     return {"value": total_rays / total_s / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+            "tiny_8x8^3_64x64_full_frame": {"seconds": round(tiny_s, 4),
+                                            "mrays_per_s": round(r0.n / tiny_s / 1e6, 4)},
             "sample": f"{total_rays} seeded random pixels of the 667x1024 frame (of 683008), FP64 oracle, "
                       f"pruned mode, {cores} OpenMP threads, {total_s:.1f} s"}
 
@@ -510,6 +517,8 @@ def run_gpu(args):
     # evaluations of one frame (the work count of the roofline)
     n_eval = int(T.raymarch_count(info["ctx"], info["prims"], info["bvh"], info["rs"]).sum().item())
     info["ctx"].sync()
+    # rays whose opacity saturated (A = 1) in the frame
+    saturated = float((info["out"][:, 3] >= 1.0).float().mean().item())
 
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s (FMA = 2)
@@ -521,6 +530,10 @@ def run_gpu(args):
                 "kernel": "k_march<f32>", "march_ms": round(march_ms, 4), "evaluations": n_eval,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
                 "gather_GBps": round(GATHER_BYTES["f32"] * n_eval / (march_ms * 1e-3) / 1e9, 1),
+                "gather_frac_of_l1_nominal": round(GATHER_BYTES["f32"] * n_eval / (march_ms * 1e-3) / 1e9 /
+                                                   (152 * 128 * sm_max * 1e6 / 1e9), 4),
+                "hbm_frac": (round(ncu["dram_bytes_per_launch"] / (march_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)
+                             if ncu.get("dram_bytes_per_launch") and peaks.get("hbm_gbs") else None),
                 "hbm_peak_GBps": peaks.get("hbm_gbs"), "hbm_peak_kind": peak_kind}
     # BVH: primitives + one-block sort (n <= 8192) or bounds, primitives and 4 radix
     # passes of 3 kernels; then hierarchy, refit; then the march
@@ -530,6 +543,7 @@ def run_gpu(args):
               "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; stands in for the paper's captures)",
               "config": {"workload": WORKLOAD, "primitives": 4096, "payload": "16^3 RGBA f32", "rays": n_rays,
                          "image": "667x1024", "dt": 0.005, "t_range": [1.0, 5.0], "samples_per_ray": 800,
+                         "saturated_ray_fraction": round(saturated, 4),
                          "step": "BVH rebuild + traversal + march", "l2": "flushed (512 MiB write) before each step",
                          "parallelism": f"replicas x{ws} (each rank its own frame)"},
               "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps}
@@ -547,6 +561,8 @@ def run_gpu(args):
         for name, cfg, dtype in (("fwd_bf16", WORKLOAD, "bf16"), ("fwd_f16", WORKLOAD, "f16"),
                                  ("fwd_f32_512x32^3", "sweep_512x32^3_667x1024", "f32"),
                                  ("fwd_f32_32768x8^3", "sweep_32768x8^3_667x1024", "f32"),
+                                 ("fwd_f32_dt0.01", "paper_4096x16^3_667x1024_dt0.01", "f32"),
+                                 ("fwd_f32_dt0.0025", "paper_4096x16^3_667x1024_dt0.0025", "f32"),
                                  ("fwd_bf16_32768x8^3", "sweep_32768x8^3_667x1024", "bf16")):
             st, nr, inf = _frame_runner(cfg, 0, dtype, False, torch, T, synthetic)
             d = _time_steps(torch, st, args.steps, args.warmup, flush, time_march=True)

@@ -264,6 +264,9 @@ CONFIGS = {
     "paper_4096x16^3_667x1024": _c1_factory(4096, 16),
     "sweep_512x32^3_667x1024": _c1_factory(512, 32),
     "sweep_32768x8^3_667x1024": _c1_factory(32768, 8),
+    # Step-size sweep of the paper-scale frame (render time grows as 1/dt).
+    "paper_4096x16^3_667x1024_dt0.01": _c1_factory(4096, 16, dt=0.01),
+    "paper_4096x16^3_667x1024_dt0.0025": _c1_factory(4096, 16, dt=0.0025),
     # Reduced shapes of the same recipe, for parity tests that the oracle finishes quickly.
     "small_512x8^3_96x128": _c1_factory(512, 8, width=96, height=128, focal=128.0),
     "small_4096x16^3_83x128": _c1_factory(4096, 16, width=83, height=128, focal=128.0),
