@@ -333,6 +333,34 @@ def _ncu_record(kernel_key: str) -> dict:
     return {}
 
 
+def _fade_pack(torch, T, synthetic, peaks):
+    """The opacity fade fused with the FP32 -> BF16 payload conversion on the
+    paper-scale payload (4096 x 16^3 voxels): 16 bytes read and 8 written per voxel,
+    against the measured HBM copy bandwidth."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sc, _, _ = synthetic.make_config(WORKLOAD, 0)
+    ctx = T.Context(dev.index)
+    p32 = torch.from_numpy(sc.payload).to(dev)
+    out = torch.empty(p32.shape, dtype=torch.bfloat16, device=dev)
+    for _ in range(3):
+        T.fade_payload(ctx, p32, torch.bfloat16, 8.0, 8, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 20
+    e0.record()
+    for _ in range(n):
+        T.fade_payload(ctx, p32, torch.bfloat16, 8.0, 8, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.sync()
+    ms = e0.elapsed_time(e1) / n
+    n_vox = p32.numel() // 4
+    gbps = 24.0 * n_vox / (ms * 1e-3) / 1e9
+    return {"ms": round(ms, 4), "GBps": round(gbps, 1),
+            "hbm_frac": round(gbps / peaks["hbm_gbs"], 3) if peaks.get("hbm_gbs") else None,
+            "bytes_per_voxel": 24, "voxels": n_vox, "workload": WORKLOAD}
+
+
 def _serve_trace(T, srv, ids, reqs, arrivals):
     """Submit `reqs` at their Poisson arrival times and poll until all are done.
     Returns (latencies in ms, wall seconds)."""
@@ -586,6 +614,7 @@ def run_gpu(args):
             "workload": "diff_512x32^3_4x512x512", "step": "BVH + forward + L2 loss grad + backward (payload + pose)"}
         del st, inf
         torch.cuda.empty_cache()
+        variants["fade_pack_bf16"] = _fade_pack(torch, T, synthetic, peaks)
         if variants.get("fwd_bf16"):
             variants["bf16_over_f32"] = round(variants["fwd_bf16"]["value"] / value, 3)
         if variants.get("e2e_bf16") and result.get("e2e"):

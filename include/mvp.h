@@ -261,6 +261,35 @@ MVP_API mvp_status mvp_serve_wait(mvp_server *server, uint64_t ticket, double ti
 /* Counters, and the kernel status bits (reads the device status word). */
 MVP_API mvp_status mvp_serve_stats(mvp_server *server, mvp_serve_info *info);
 
+/* ------------------------------------------------ decode-side epilogues */
+/* The steps just upstream of the march that turn a decoder's outputs into march
+ * inputs, and their gradients. All asynchronous on `stream`.
+ *
+ * Opacity fade (Sec. 3.1.3): dst = src with the opacity (channel 3) of every voxel
+ * multiplied by W(x,y,z) = exp(-alpha (x^beta + y^beta + z^beta)), (x,y,z) in [-1,1]^3
+ * the voxel's corner-aligned coordinates 2 (i, j, l)/(M - 1) - 1 (the paper uses
+ * alpha = beta = 8; beta in [0, 64] is an integer). src: [n_prims][M][M][M][4] FP32
+ * device; dst: the same layout in `dtype` (FP32, BF16 or FP16, round to nearest even),
+ * so the fade is fused into the precision conversion. dst may equal src only for
+ * FP32 output; other overlaps are rejected. Applied to a payload gradient (FP32, in
+ * place) it gives the gradient with respect to the unfaded opacity. */
+MVP_API mvp_status mvp_fade_payload(mvp_ctx *ctx, const float *src, void *dst, int64_t n_prims, int32_t M,
+                                    int32_t dtype, float alpha, int32_t beta, mvp_stream stream);
+/* Rotation from an axis-angle (Rodrigues) vector (Sec. 3.1.2: the paper's rotation
+ * parameterisation): q = (cos(th/2), sin(th/2) r/th), th = |r| (q = (1, 0, 0, 0) at
+ * r = 0). r [n][3], q [n][4] FP32 device; q feeds mvp_prims.q. */
+MVP_API mvp_status mvp_axis_angle_to_quat(mvp_ctx *ctx, const float *r, int32_t n, float *q, mvp_stream stream);
+/* Its vector-Jacobian product: g_r [n][3] += (dq/dr)^T g_q [n][4] (FP32 device), to
+ * chain a g_q from mvp_raymarch_bwd to the axis-angle parameters. */
+MVP_API mvp_status mvp_axis_angle_backward(mvp_ctx *ctx, const float *r, const float *g_q, int32_t n, float *g_r,
+                                           mvp_stream stream);
+/* Volume minimisation prior (Sec. 3.3): L_vol = lambda sum_k prod_j (2 s_kj), the
+ * summed volumes with side lengths twice the half extents s [n][3] (FP32 device);
+ * the paper uses lambda = 0.01. loss (device float, nullable) += L_vol; g_s (device
+ * [n][3], nullable) += dL_vol/ds. */
+MVP_API mvp_status mvp_volume_prior(mvp_ctx *ctx, const float *s, int32_t n, float lambda, float *loss, float *g_s,
+                                    mvp_stream stream);
+
 /* ------------------------------------------------ allocation-free render */
 /* No counterpart in the paper. For callers that cannot allocate device memory:
  * a plug-in inside a host application that owns every device allocation, a

@@ -93,6 +93,11 @@ _SIGS = [
     ("mvp_serve_stats", c_int32, [c_void_p, ctypes.POINTER(mvp_serve_info)]),
     ("mvp_raymarch_fwd_static", c_int32, [ctypes.POINTER(mvp_prims), ctypes.POINTER(mvp_rays), c_void_p, c_void_p,
                                           c_void_p]),
+    ("mvp_fade_payload", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_float, c_int32,
+                                   c_void_p]),
+    ("mvp_axis_angle_to_quat", c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    ("mvp_axis_angle_backward", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    ("mvp_volume_prior", c_int32, [c_void_p, c_void_p, c_int32, c_float, c_void_p, c_void_p, c_void_p]),
 ]
 
 

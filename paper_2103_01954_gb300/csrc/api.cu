@@ -401,4 +401,59 @@ mvp_status mvp_camera_rays(mvp_ctx *ctx, const float *c2w, float focal, int32_t 
   return ok();
 }
 
+// ---------------------------------------------------------------- decode-side epilogues
+mvp_status mvp_fade_payload(mvp_ctx *ctx, const float *src, void *dst, int64_t n_prims, int32_t M, int32_t dtype,
+                            float alpha, int32_t beta, mvp_stream stream) {
+  if (!ctx) return fail(MVP_ERR_INVALID_ARG, "ctx is NULL");
+  if (n_prims < 0 || n_prims > MVP_MAX_PRIMS) return fail(MVP_ERR_INVALID_ARG, "n_prims out of range");
+  if (M < 2 || M > MVP_MAX_M) return fail(MVP_ERR_INVALID_ARG, "M out of [2, %d]", MVP_MAX_M);
+  if (dtype != MVP_F32 && dtype != MVP_BF16 && dtype != MVP_F16) return fail(MVP_ERR_INVALID_ARG, "dtype unknown");
+  if (!finite(alpha) || beta < 0 || beta > 64) return fail(MVP_ERR_INVALID_ARG, "alpha not finite or beta out of [0, 64]");
+  if (n_prims > 0 && (!src || !dst)) return fail(MVP_ERR_INVALID_ARG, "NULL buffer");
+  const size_t nv = (size_t)n_prims * M * M * M;
+  if (reinterpret_cast<uintptr_t>(src) % 16 || reinterpret_cast<uintptr_t>(dst) % (dtype == MVP_F32 ? 16 : 8))
+    return fail(MVP_ERR_INVALID_ARG, "misaligned buffer");
+  if (dtype != MVP_F32 && n_prims > 0) {
+    const char *a = reinterpret_cast<const char *>(src), *b = reinterpret_cast<const char *>(dst);
+    if (a < b + nv * 8 && b < a + nv * 16) return fail(MVP_ERR_INVALID_ARG, "src and dst overlap (only FP32 may be in place)");
+  }
+  DeviceGuard g(ctx->device);
+  cudaError_t e = mvp::launch_fade(src, dst, n_prims, M, dtype, alpha, beta, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "fade launch");
+  return ok();
+}
+
+mvp_status mvp_axis_angle_to_quat(mvp_ctx *ctx, const float *r, int32_t n, float *q, mvp_stream stream) {
+  if (!ctx) return fail(MVP_ERR_INVALID_ARG, "ctx is NULL");
+  if (n < 0) return fail(MVP_ERR_INVALID_ARG, "n < 0");
+  if (n > 0 && (!r || !q)) return fail(MVP_ERR_INVALID_ARG, "NULL buffer");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = mvp::launch_aa_to_quat(r, n, q, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "axis-angle launch");
+  return ok();
+}
+
+mvp_status mvp_axis_angle_backward(mvp_ctx *ctx, const float *r, const float *g_q, int32_t n, float *g_r,
+                                   mvp_stream stream) {
+  if (!ctx) return fail(MVP_ERR_INVALID_ARG, "ctx is NULL");
+  if (n < 0) return fail(MVP_ERR_INVALID_ARG, "n < 0");
+  if (n > 0 && (!r || !g_q || !g_r)) return fail(MVP_ERR_INVALID_ARG, "NULL buffer");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = mvp::launch_aa_vjp(r, g_q, n, g_r, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "axis-angle gradient launch");
+  return ok();
+}
+
+mvp_status mvp_volume_prior(mvp_ctx *ctx, const float *s, int32_t n, float lambda, float *loss, float *g_s,
+                            mvp_stream stream) {
+  if (!ctx) return fail(MVP_ERR_INVALID_ARG, "ctx is NULL");
+  if (n < 0) return fail(MVP_ERR_INVALID_ARG, "n < 0");
+  if (!finite(lambda)) return fail(MVP_ERR_INVALID_ARG, "lambda not finite");
+  if (n > 0 && !s) return fail(MVP_ERR_INVALID_ARG, "s is NULL");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = mvp::launch_volume_prior(s, n, lambda, loss, g_s, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "volume prior launch");
+  return ok();
+}
+
 }  // extern "C"

@@ -177,6 +177,47 @@ def pack_payload(ctx: Context, payload_f32: torch.Tensor, dtype: torch.dtype) ->
     return out
 
 
+def fade_payload(ctx: Context, payload_f32: torch.Tensor, dtype: torch.dtype = torch.float32, alpha: float = 8.0,
+                 beta: int = 8, out: torch.Tensor | None = None) -> torch.Tensor:
+    """mvp_fade_payload: opacity multiplied by the fade window, converted to `dtype`.
+    payload_f32 is [n, M, M, M, 4]; out may be payload_f32 itself when dtype is FP32."""
+    _need(payload_f32, "payload", torch.float32)
+    n, M = payload_f32.shape[0], payload_f32.shape[1]
+    if out is None:
+        out = torch.empty(payload_f32.shape, dtype=dtype, device=payload_f32.device)
+    B.check(B.lib().mvp_fade_payload(ctx.handle, _ptr(payload_f32), _ptr(out), n, M, _DT[dtype], float(alpha),
+                                     int(beta), _stream()), "mvp_fade_payload")
+    return out
+
+
+def axis_angle_to_quat(ctx: Context, r: torch.Tensor) -> torch.Tensor:
+    _need(r, "r", torch.float32, (3,))
+    q = torch.empty((r.shape[0], 4), dtype=torch.float32, device=r.device)
+    B.check(B.lib().mvp_axis_angle_to_quat(ctx.handle, _ptr(r), r.shape[0], _ptr(q), _stream()),
+            "mvp_axis_angle_to_quat")
+    return q
+
+
+def axis_angle_backward(ctx: Context, r: torch.Tensor, g_q: torch.Tensor, g_r: torch.Tensor | None = None):
+    """g_r += (dq/dr)^T g_q; returns g_r."""
+    _need(r, "r", torch.float32, (3,))
+    _need(g_q, "g_q", torch.float32, (4,))
+    if g_r is None:
+        g_r = torch.zeros_like(r)
+    B.check(B.lib().mvp_axis_angle_backward(ctx.handle, _ptr(r), _ptr(g_q), r.shape[0], _ptr(g_r), _stream()),
+            "mvp_axis_angle_backward")
+    return g_r
+
+
+def volume_prior(ctx: Context, s: torch.Tensor, lam: float = 0.01, g_s: torch.Tensor | None = None):
+    """Returns (loss tensor [1], g_s) with g_s += dL_vol/ds (g_s None: no gradient)."""
+    _need(s, "s", torch.float32, (3,))
+    loss = torch.zeros(1, dtype=torch.float32, device=s.device)
+    B.check(B.lib().mvp_volume_prior(ctx.handle, _ptr(s), s.shape[0], float(lam), _ptr(loss), _ptr(g_s),
+                                     _stream()), "mvp_volume_prior")
+    return loss, g_s
+
+
 def camera_rays(ctx: Context, c2w, focal: float, width: int, height: int):
     dev = torch.device("cuda", ctx.device)
     o = torch.empty((width * height, 3), dtype=torch.float32, device=dev)
