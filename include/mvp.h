@@ -216,11 +216,16 @@ typedef struct mvp_server mvp_server;
 
 typedef struct mvp_request {
   int32_t avatar;        /* id from mvp_serve_register_avatar */
-  int32_t width, height; /* image size in pixels (>= 1) */
+  int32_t width, height; /* image size in pixels (>= 1), per view */
   float focal;           /* pixels */
   float c2w[12];         /* row-major 3x4 [right down forward | eye], as mvp_camera_rays */
   float t_near, t_far, dt, eps_early;
   float bg[3];
+  int32_t views;         /* 1 (0 counts as 1), or 2: a stereo pair (the paper's binocular
+                          * viewer, Sec. 4) rendered from one BVH in one launch; the image
+                          * is then [2][height][width][4], view 0 from c2w, view 1 from
+                          * c2w_right */
+  float c2w_right[12];   /* second view's camera (views = 2) */
 } mvp_request;
 
 typedef struct mvp_serve_info {

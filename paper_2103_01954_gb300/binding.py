@@ -40,7 +40,7 @@ class mvp_rays(ctypes.Structure):
 class mvp_request(ctypes.Structure):
     _fields_ = [("avatar", c_int32), ("width", c_int32), ("height", c_int32), ("focal", c_float),
                 ("c2w", c_float * 12), ("t_near", c_float), ("t_far", c_float), ("dt", c_float),
-                ("eps_early", c_float), ("bg", c_float * 3)]
+                ("eps_early", c_float), ("bg", c_float * 3), ("views", c_int32), ("c2w_right", c_float * 12)]
 
 
 class mvp_serve_info(ctypes.Structure):

@@ -2,7 +2,8 @@
 // and resolutions) on one GPU.
 //
 // Device side. Each admitted request is one launch of k_serve, its arguments in the
-// kernel's parameter block, with one warp per 8x4-pixel tile of its image. A warp
+// kernel's parameter block, with one warp per 8x4-pixel tile of its image (of both
+// images for a stereo pair, which share the avatar's BVH and one launch). A warp
 // generates its tile's pinhole rays and marches them with the same code as
 // mvp_raymarch_fwd (march_tile, specialised for M = 8, 16, 32 and for the payload
 // type). Nothing on the device ever waits. The warp that counts a request's last
@@ -46,6 +47,8 @@ struct ReqDone {
 struct ServeReq {
   MarchArgs m;               // payload, BVH, sampling, output image (m.o, m.d unused)
   float c2w[12];
+  float c2w2[12];            // second view (views = 2)
+  int views;                 // 1 or 2; the image is [views][height][width][4]
   float focal;
   int slot;                  // completion record and tile counter index
   unsigned long long seq;    // request sequence number
@@ -73,21 +76,24 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, MVP_MARCH_MINB) k_serve(const
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   TileShared<SERVE_CAP> &sh = reinterpret_cast<TileShared<SERVE_CAP> *>(smem_raw)[warp];
   const int64_t wt = (int64_t)blockIdx.x * TILE_WARPS + warp;
-  const int64_t n_tiles = R.m.geom.n_warp_tiles;
+  const int64_t n_view = R.m.geom.n_warp_tiles;  // tiles per view
+  const int64_t n_tiles = n_view * R.views;
   if (wt >= n_tiles) return;
   if (lane == 0 && wt == 0) R.done[R.slot].t_start_ns = globaltimer();
+  // a stereo request's tiles run through view 0, then view 1 (a tile never spans both)
+  const int view = wt >= n_view ? 1 : 0;
   LaneRay L;
-  const int64_t r = tile_ray(R.m.geom, wt, lane);
-  L.r = r;
+  const int64_t r = tile_ray(R.m.geom, wt - view * n_view, lane);
+  L.r = r >= 0 ? r + view * R.m.geom.n_rays : -1;  // pixel of the [views][h][w] image
   if (r >= 0) {
     const int width = R.m.geom.width;
     const int row = (int)(r / width), col = (int)(r - (int64_t)row * width);
-    camera_ray(R.c2w, R.focal, width, R.m.geom.height, row, col, L.o, L.d);
+    camera_ray(view ? R.c2w2 : R.c2w, R.focal, width, R.m.geom.height, row, col, L.o, L.d);
   } else {
 #pragma unroll
     for (int j = 0; j < 3; ++j) L.o[j] = L.d[j] = 0.0f;
   }
-  if (__ballot_sync(FULL, r >= 0) != 0) march_tile<DT, SERVE_CAP, false, MT>(sh, R.m, L);
+  if (__ballot_sync(FULL, L.r >= 0) != 0) march_tile<DT, SERVE_CAP, false, MT>(sh, R.m, L);
   __syncwarp();
   if (lane == 0) {
     __threadfence();  // this tile's pixels are visible before it is counted
@@ -217,7 +223,11 @@ mvp_status serve_fail(mvp_status s, const char *msg) {
   return s;
 }
 
-size_t image_bytes(const mvp_request &r) { return (size_t)r.width * (size_t)r.height * 4 * sizeof(float); }
+int request_views(const mvp_request &r) { return r.views == 2 ? 2 : 1; }
+
+size_t image_bytes(const mvp_request &r) {
+  return (size_t)request_views(r) * (size_t)r.width * (size_t)r.height * 4 * sizeof(float);
+}
 
 // Launch one admitted request on the stream with the fewest requests outstanding
 // (round robin among ties): its image's warp tiles run as soon as SMs free up,
@@ -245,6 +255,8 @@ mvp_status launch(mvp_server *S, InFlight &f) {
   m.out = reinterpret_cast<float *>(S->arena_base + f.off);
   m.status = S->d_status;
   memcpy(R.c2w, q.c2w, sizeof(R.c2w));
+  memcpy(R.c2w2, q.c2w_right, sizeof(R.c2w2));
+  R.views = request_views(q);
   R.focal = q.focal;
   R.slot = f.slot;
   R.seq = f.seq;
@@ -256,7 +268,7 @@ mvp_status launch(mvp_server *S, InFlight &f) {
     if (best < 0 || S->outstanding[i] < S->outstanding[best]) best = i;
   }
   S->next_stream = (best + 1) % mvp::SERVE_STREAMS;
-  const unsigned blocks = (unsigned)(m.geom.n_warp_tiles / mvp::TILE_WARPS);
+  const unsigned blocks = (unsigned)(m.geom.n_warp_tiles * R.views / mvp::TILE_WARPS);
   mvp::k_serve_table[mvp::serve_class(m.dtype, m.M)]<<<blocks, mvp::TILE_WARPS * 32, S->smem, S->streams[best]>>>(R);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return serve_fail(MVP_ERR_CUDA, cudaGetErrorString(e));
@@ -415,13 +427,15 @@ mvp_status mvp_serve_submit(mvp_server *S, const mvp_request *req, uint64_t *tic
   std::lock_guard<std::mutex> lk(S->mu);
   if (req->avatar < 0 || req->avatar >= (int32_t)S->avatars.size())
     return serve_fail(MVP_ERR_INVALID_ARG, "unknown avatar");
+  if (req->views < 0 || req->views > 2) return serve_fail(MVP_ERR_INVALID_ARG, "views must be 1 or 2");
   if (req->width < 1 || req->height < 1 || (int64_t)req->width * req->height > (int64_t)1 << 30 ||
       !(req->focal > 0.0f) || !(req->dt > 0.0f) || !(req->t_far > req->t_near) ||
       !(req->eps_early >= 0.0f && req->eps_early < 1.0f) ||
       mvp_num_steps(req->t_near, req->t_far, req->dt) > MVP_MAX_STEPS)
     return serve_fail(MVP_ERR_INVALID_ARG, "bad request parameters");
   for (int i = 0; i < 12; ++i)
-    if (!isfinite(req->c2w[i])) return serve_fail(MVP_ERR_INVALID_ARG, "camera must be finite");
+    if (!isfinite(req->c2w[i]) || (req->views == 2 && !isfinite(req->c2w_right[i])))
+      return serve_fail(MVP_ERR_INVALID_ARG, "camera must be finite");
   const size_t bytes = image_bytes(*req);
   if (S->resident + bytes > S->budget || ((bytes + 255) & ~size_t(255)) > S->arena.size)
     return serve_fail(MVP_ERR_CAPACITY, "request image exceeds the HBM budget");

@@ -288,11 +288,15 @@ class Server:
 
     @staticmethod
     def request(avatar: int, c2w, focal: float, width: int, height: int, t_near: float, t_far: float, dt: float,
-                eps_early: float = 0.0, bg=(0.0, 0.0, 0.0)) -> B.mvp_request:
+                eps_early: float = 0.0, bg=(0.0, 0.0, 0.0), c2w_right=None) -> B.mvp_request:
+        """A request; with c2w_right, a stereo pair whose image is [2][height][width][4]."""
         r = B.mvp_request(avatar=avatar, width=width, height=height, focal=focal, t_near=t_near, t_far=t_far, dt=dt,
-                          eps_early=eps_early)
+                          eps_early=eps_early, views=1 if c2w_right is None else 2)
         for i, v in enumerate([float(x) for x in list(c2w.reshape(-1))]):
             r.c2w[i] = v
+        if c2w_right is not None:
+            for i, v in enumerate([float(x) for x in list(c2w_right.reshape(-1))]):
+                r.c2w_right[i] = v
         r.bg[0], r.bg[1], r.bg[2] = bg
         return r
 

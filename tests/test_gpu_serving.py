@@ -149,3 +149,33 @@ def test_wait_timeout_unknown_ticket_and_bad_avatar():
         srv.submit_raw(T.Server.request(7, cams[0], 32.0, w, h, T_NEAR, T_FAR, DT))
     assert ei.value.status == B.MVP_ERR_INVALID_ARG
     srv.close()
+
+
+def test_stereo_request_equals_two_mono_requests():
+    """A binocular request (two cameras, one launch, the avatar's one BVH) gives, per
+    eye, the image of the corresponding mono request, bit for bit."""
+    torch.cuda.set_device(0)
+    ctx = T.Context(0)
+    avs = _avatars(ctx)
+    srv = T.Server(ctx, hbm_budget=2 << 30, max_slots=8)
+    ids = [srv.register(*a) for a in avs]
+    w, h = 72, 56  # ragged tiles in both directions
+    cam = _cams(1, 11)[0]
+    right = cam.copy()
+    right[:, 3] += 0.064 * right[:, 0]  # eye moved 6.4 cm along the camera's right axis
+    for aid, av in zip(ids, avs):
+        tk = srv.submit_raw(T.Server.request(aid, cam, float(w), w, h, T_NEAR, T_FAR, DT, c2w_right=right))
+        both = torch.empty((2, h * w, 4), dtype=torch.float32, device=DEV)
+        st, _ = srv.wait(tk, 10000.0, both)
+        assert st == B.MVP_OK
+        for eye, c in ((0, cam), (1, right)):
+            tk = srv.submit_raw(T.Server.request(aid, c, float(w), w, h, T_NEAR, T_FAR, DT))
+            mono = torch.empty((h * w, 4), dtype=torch.float32, device=DEV)
+            st, _ = srv.wait(tk, 10000.0, mono)
+            assert st == B.MVP_OK
+            assert torch.equal(both[eye], mono)
+            ref = _reference(ctx, av, c, float(w), w, h)
+            assert (mono - ref).abs().max().item() <= 1e-5
+        assert not torch.equal(both[0], both[1])  # the eyes see different images
+    assert srv.stats()["device_status"] == 0
+    srv.close()
