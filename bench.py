@@ -119,8 +119,9 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def _frame_runner(cfg: str, seed: int, dtype: str, want_bwd: bool, torch, T, synthetic):
-    """Set up a workload on the device; returns (step(), n_rays, info)."""
+def _frame_runner(cfg: str, seed: int, dtype: str, want_bwd: bool, torch, T, synthetic, sequential=False):
+    """Set up a workload on the device; returns (step(), n_rays, info). sequential:
+    blend each ray's saturating sample in BVH order (MVP_BLEND_SEQUENTIAL)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     scene, rays, extra = synthetic.make_config(cfg, seed)
     ctx = T.Context(dev.index)
@@ -136,7 +137,7 @@ def _frame_runner(cfg: str, seed: int, dtype: str, want_bwd: bool, torch, T, syn
     d = torch.from_numpy(rays.d).to(dev)
     prims = T.prims_struct(t, q, s, payload)
     rs = T.rays_struct(o, d, t_near=rays.t_near, t_far=rays.t_far, dt=rays.dt, eps_early=rays.eps_early,
-                       bg=tuple(rays.bg), width=rays.width, height=rays.height)
+                       bg=tuple(rays.bg), width=rays.width, height=rays.height, sequential=sequential)
     bvh = T.BVH(ctx)
     bvh.build(prims)
     out = torch.empty((rays.n, 4), dtype=torch.float32, device=dev)
@@ -149,8 +150,11 @@ def _frame_runner(cfg: str, seed: int, dtype: str, want_bwd: bool, torch, T, syn
         grad_out = torch.zeros((rays.n, 4), dtype=torch.float32, device=dev)
         grads = (gp, gt, gq, gs, grad_out, target)
     ev = {"march": []}
+    # the ABI structs hold raw device pointers: the step keeps their tensors alive
+    keep = (t, q, s, payload, o, d)
 
     def step(time_march=False):
+        assert keep
         bvh.build(prims)
         if time_march:
             e0 = torch.cuda.Event(enable_timing=True)
@@ -167,7 +171,7 @@ def _frame_runner(cfg: str, seed: int, dtype: str, want_bwd: bool, torch, T, syn
             gp.zero_(), gt.zero_(), gq.zero_(), gs.zero_()
             T.raymarch_bwd(ctx, prims, bvh, rs, saved, grad_out, gp, gt, gq, gs)
 
-    info = {"scene": scene, "rays": rays, "ctx": ctx, "prims": prims, "bvh": bvh, "rs": rs, "ev": ev,
+    info = {"scene": scene, "rays": rays, "ctx": ctx, "prims": prims, "bvh": bvh, "rs": rs, "ev": ev, "o": o, "d": d, "keep": keep,
             "payload_bytes": payload.numel() * payload.element_size(), "out": out,
             "host": (scene, rays), "n_prims": int(scene.t.shape[0])}
     return step, rays.n, info
@@ -331,6 +335,33 @@ def _ncu_record(kernel_key: str) -> dict:
     except Exception:
         return {}
     return {}
+
+
+def _sequential_blend(torch, T, synthetic, args, flush):
+    """The headline frame with the paper-literal blend (the primitives at a ray's
+    saturating sample taken one by one in BVH order): its rate, and how far its image
+    is from the summed rule's on the same frame."""
+    st, nr, inf = _frame_runner(WORKLOAD, 0, "f32", False, torch, T, synthetic, sequential=True)
+    d = _time_steps(torch, st, args.steps, args.warmup, flush, time_march=True)
+    inf["ctx"].sync()
+    m = float(np.mean(d))
+    mm = float(np.mean([a.elapsed_time(b) for a, b in inf["ev"]["march"]]))
+    seq = inf["out"].clone()
+    r = inf["rays"]
+    rs = T.rays_struct(inf["o"], inf["d"], t_near=r.t_near, t_far=r.t_far, dt=r.dt, eps_early=r.eps_early,
+                       bg=tuple(r.bg), width=r.width, height=r.height)
+    summ = torch.empty_like(seq)
+    T.raymarch_fwd(inf["ctx"], inf["prims"], inf["bvh"], rs, out=summ)
+    inf["ctx"].sync()
+    diff = (seq - summ).abs().amax(dim=1)
+    out = {"value": round(nr / (m * 1e-3) / 1e6, 3), "unit": "Mrays/s", "ms_per_step": round(m, 4),
+           "march_ms": round(mm, 4), "workload": WORKLOAD, "payload_dtype": "f32",
+           "pixels_differing_from_summed_1e-3": round(float((diff > 1e-3).float().mean()), 4),
+           "max_abs_diff_from_summed": round(float(diff.max()), 5),
+           "alpha_max_abs_diff": float((seq[:, 3] - summ[:, 3]).abs().max())}
+    del st, inf, seq, summ
+    torch.cuda.empty_cache()
+    return out
 
 
 def _vr_stereo(torch, T, synthetic, flush, steps=20):
@@ -651,6 +682,7 @@ def run_gpu(args):
                 variants["e2e_bf16"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in e.items()}
             del st, inf
             torch.cuda.empty_cache()
+        variants["fwd_f32_sequential"] = _sequential_blend(torch, T, synthetic, args, flush)
         st, nr, inf = _frame_runner("diff_512x32^3_4x512x512", 0, "f32", True, torch, T, synthetic)
         d = _time_steps(torch, st, args.steps, args.warmup, flush)
         inf["ctx"].sync()

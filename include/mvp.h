@@ -103,7 +103,15 @@ typedef struct mvp_rays {
   float bg[3];          /* constant background colour */
   int32_t width;        /* if width * height == n: rays form a row-major image  */
   int32_t height;       /* and are marched in 2-D pixel tiles; else 1-D groups  */
+  int32_t flags;        /* 0, or MVP_BLEND_SEQUENTIAL */
 } mvp_rays;
+
+/* mvp_rays.flags: blend the primitives that share a ray's saturating sample one by
+ * one in BVH order (the order of their leaves: ascending (morton << 32 | k)), as the
+ * paper describes for overlapping primitives (Sec. 3.2.2), instead of summing them and
+ * clamping once. Every other sample is unaffected (the two rules agree wherever T
+ * stays below 1). Forward only: mvp_raymarch_bwd rejects it. */
+#define MVP_BLEND_SEQUENTIAL 1
 
 typedef struct mvp_ctx mvp_ctx;
 typedef struct mvp_bvh mvp_bvh;

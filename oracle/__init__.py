@@ -17,4 +17,5 @@ from .oracle import (  # noqa: F401
     MODE_PRUNED,
     MEMBER_F64,
     MEMBER_F32,
+    SEQUENTIAL,
 )

@@ -37,7 +37,12 @@
  *   R1 quadrature: left Riemann sum on t_i = t_near + i*dt, i in [0, n_steps);
  *      per sample a = dt*sum_k alpha_k, c = dt*sum_k alpha_k*rgb_k,
  *      w = min(a, 1 - T), I += c*w/a, T += w  (T = min(sum a, 1) exactly).
- *   R2 several primitives at one sample: summed, then clamped once.
+ *   R2 several primitives at one sample: summed, then clamped once. The paper's
+ *      literal rule, each primitive in turn in BVH order, is mode bit2
+ *      (ORC_SEQUENTIAL): it differs only at a ray's saturating sample, where the
+ *      primitives containing it are taken in the order of their Morton keys (the
+ *      leaf order of the Karras hierarchy), each adding w_k = min(dt alpha_k, 1 - T)
+ *      of its colour until T = 1.
  *   R3 s_k are half extents: x = t_k + R_k diag(s_k) y with y in [-1,1]^3.
  *   R4 corner-aligned voxels: u = (y+1)/2*(M-1), cell i0 = min(floor(u), M-2).
  *   R5 I_p is already weighted by dT, so the background composite is
@@ -291,7 +296,16 @@ typedef struct {
   double *R64;
   float *R32;
   float *U32; /* [n][3][4] FP32 voxel-coordinate rows, see voxel_coord_f32 */
+  int *rank;  /* position of each primitive in the sorted Morton keys (mode bit2), or NULL */
 } scene_t;
+
+#define ORC_SEQUENTIAL 4
+
+/* One primitive's trilinear RGBA at the current sample (sequential blending). */
+typedef struct {
+  int k;
+  double v[4];
+} seq_t;
 
 typedef struct {
   const float *o, *d;
@@ -452,10 +466,12 @@ static int member(const scene_t *sc, const cand_t *c, int brute_k, int f32m, flo
 }
 
 /* March one ray (R1, R2). mode bit0: 1 = pruned (per-ray candidate list), 0 = brute
- * (every primitive at every sample). mode bit1: 1 = FP32 membership decision. */
+ * (every primitive at every sample). mode bit1: 1 = FP32 membership decision.
+ * mode bit2: sequential BVH-order blending at the saturating sample (needs sc->rank
+ * and a buffer seq of n entries). */
 static void march_ray(const scene_t *sc, const march_t *m, int64_t r, int mode, cand_t *cands,
-                      ray_out_t *res) {
-  int pruned = mode & 1, f32m = (mode >> 1) & 1;
+                      seq_t *seq, ray_out_t *res) {
+  int pruned = mode & 1, f32m = (mode >> 1) & 1, sequential = (mode & ORC_SEQUENTIAL) && seq && sc->rank;
   int nc = 0;
   if (pruned || f32m) nc = ray_candidates(sc, m, r, cands);
   const float *o = m->o + 3 * r, *d = m->d + 3 * r;
@@ -472,6 +488,7 @@ static void march_ray(const scene_t *sc, const march_t *m, int64_t r, int mode, 
     double ti = f32m ? (double)ti32 : (double)m->t_near + (double)i * (double)m->dt;
     double x[3] = {o[0] + ti * d[0], o[1] + ti * d[1], o[2] + ti * d[2]};
     double a = 0.0, c[3] = {0, 0, 0};
+    int n_in = 0;
     for (int e = 0; e < nk; ++e) {
       double y[3];
       int in;
@@ -496,6 +513,11 @@ static void march_ray(const scene_t *sc, const march_t *m, int64_t r, int mode, 
       a += v[3];
       c[0] += v[3] * v[0]; c[1] += v[3] * v[1]; c[2] += v[3] * v[2];
       res->n_eval++;
+      if (sequential) {
+        seq[n_in].k = k;
+        for (int ch = 0; ch < 4; ++ch) seq[n_in].v[ch] = v[ch];
+        ++n_in;
+      }
     }
     a *= m->dt;
     c[0] *= m->dt; c[1] *= m->dt; c[2] *= m->dt;
@@ -503,6 +525,23 @@ static void march_ray(const scene_t *sc, const march_t *m, int64_t r, int mode, 
     if (a <= rem) {
       I[0] += c[0]; I[1] += c[1]; I[2] += c[2];
       T += a;
+    } else if (sequential) {
+      /* the saturating sample, primitive by primitive in BVH order (insertion sort
+       * by rank, then w_k = min(dt alpha_k, 1 - T)) */
+      for (int x1 = 1; x1 < n_in; ++x1) {
+        seq_t cur = seq[x1];
+        int y1 = x1 - 1;
+        while (y1 >= 0 && sc->rank[seq[y1].k] > sc->rank[cur.k]) { seq[y1 + 1] = seq[y1]; --y1; }
+        seq[y1 + 1] = cur;
+      }
+      for (int e = 0; e < n_in && rem > 0.0; ++e) {
+        double w = m->dt * seq[e].v[3];
+        if (w > rem) w = rem;
+        I[0] += seq[e].v[0] * w; I[1] += seq[e].v[1] * w; I[2] += seq[e].v[2] * w;
+        rem -= w;
+      }
+      res->i_clamp = i;
+      T = 1.0;
     } else {
       double beta = rem / a;
       I[0] += c[0] * beta; I[1] += c[1] * beta; I[2] += c[2] * beta;
@@ -520,6 +559,7 @@ static void march_ray(const scene_t *sc, const march_t *m, int64_t r, int mode, 
 static int scene_init(scene_t *sc, int n, int M, const float *t, const float *q, const float *s,
                       const float *payload) {
   sc->n = n; sc->M = M; sc->t = t; sc->q = q; sc->s = s; sc->payload = payload;
+  sc->rank = NULL;
   sc->R64 = (double *)malloc(sizeof(double) * 9 * (size_t)(n > 0 ? n : 1));
   sc->R32 = (float *)malloc(sizeof(float) * 9 * (size_t)(n > 0 ? n : 1));
   sc->U32 = (float *)malloc(sizeof(float) * 12 * (size_t)(n > 0 ? n : 1));
@@ -532,7 +572,28 @@ static int scene_init(scene_t *sc, int n, int M, const float *t, const float *q,
   return 0;
 }
 
-static void scene_free(scene_t *sc) { free(sc->R64); free(sc->R32); free(sc->U32); }
+static void scene_free(scene_t *sc) { free(sc->R64); free(sc->R32); free(sc->U32); free(sc->rank); }
+
+static int cmp_u64(const void *a, const void *b) {
+  uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+  return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* BVH order: rank[k] = position of primitive k's (unique) Morton key in ascending
+ * order, i.e. its leaf position in the Karras hierarchy. */
+static int scene_rank(scene_t *sc) {
+  int n = sc->n;
+  size_t nb = (size_t)(n > 0 ? n : 1);
+  uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * nb);
+  sc->rank = (int *)malloc(sizeof(int) * nb);
+  if (!keys || !sc->rank) { free(keys); return -1; }
+  float b6[6];
+  orc_morton_keys(n, sc->t, b6, keys);
+  qsort(keys, (size_t)n, sizeof(uint64_t), cmp_u64);
+  for (int i = 0; i < n; ++i) sc->rank[(uint32_t)(keys[i] & 0xffffffffu)] = i;
+  free(keys);
+  return 0;
+}
 
 /* Render: out[r] = (I + (1 - A) bg, A) (R5); near_face, n_eval and the adjoint
  * state (i_last, i_clamp, rho, beta) are optional. Returns 0, or -1 on bad input. */
@@ -544,16 +605,21 @@ int orc_render(int n, int M, const float *t, const float *q, const float *s, con
   scene_t sc;
   if (scene_init(&sc, n, M, t, q, s, payload)) return -1;
   march_t m = {o, d, t_near, t_far, dt, eps, {bg[0], bg[1], bg[2]}, n_steps};
+  if ((mode & ORC_SEQUENTIAL) && scene_rank(&sc)) {
+    scene_free(&sc);
+    return -1;
+  }
 #ifdef _OPENMP
   if (n_threads > 0) omp_set_num_threads(n_threads);
 #endif
 #pragma omp parallel
   {
     cand_t *cands = (cand_t *)malloc(sizeof(cand_t) * (size_t)(n > 0 ? n : 1));
+    seq_t *seq = (seq_t *)malloc(sizeof(seq_t) * (size_t)(n > 0 ? n : 1));
 #pragma omp for schedule(dynamic, 16)
     for (int64_t r = 0; r < n_rays; ++r) {
       ray_out_t res;
-      march_ray(&sc, &m, r, mode, cands, &res);
+      march_ray(&sc, &m, r, mode, cands, seq, &res);
       double A = res.T;
       for (int c = 0; c < 3; ++c) out[4 * r + c] = res.rgb[c] + (1.0 - A) * (double)bg[c];
       out[4 * r + 3] = A;
@@ -563,6 +629,7 @@ int orc_render(int n, int M, const float *t, const float *q, const float *s, con
       if (i_clamp) i_clamp[r] = res.i_clamp;
     }
     free(cands);
+    free(seq);
   }
   scene_free(&sc);
   return 0;
@@ -610,6 +677,7 @@ int orc_backward(int n, int M, const float *t, const float *q, const float *s, c
                  float eps, const float *bg, int n_steps, int mode, int n_threads,
                  const double *grad_out, double *g_payload, double *g_t, double *g_q, double *g_s) {
   if (n < 0 || M < 2 || n_rays < 0 || !(dt > 0) || n_steps < 0) return -1;
+  if (mode & ORC_SEQUENTIAL) return -1; /* the adjoint follows the summed rule only */
   scene_t sc;
   if (scene_init(&sc, n, M, t, q, s, payload)) return -1;
   march_t m = {o, d, t_near, t_far, dt, eps, {bg[0], bg[1], bg[2]}, n_steps};
@@ -624,7 +692,7 @@ int orc_backward(int n, int M, const float *t, const float *q, const float *s, c
 #pragma omp for schedule(dynamic, 16)
     for (int64_t r = 0; r < n_rays; ++r) {
       ray_out_t res;
-      march_ray(&sc, &m, r, mode, cands, &res);
+      march_ray(&sc, &m, r, mode & ~ORC_SEQUENTIAL, cands, NULL, &res);
       int nc = (pruned || f32m) ? ray_candidates(&sc, &m, r, cands) : 0;
       const double *go = grad_out + 4 * r;
       double gI[3] = {go[0], go[1], go[2]};

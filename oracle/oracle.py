@@ -19,6 +19,7 @@ MODE_BRUTE = 0
 MODE_PRUNED = 1
 MEMBER_F64 = 0
 MEMBER_F32 = 2
+SEQUENTIAL = 4  # the saturating sample blended primitive by primitive in BVH order
 
 _lib = None
 

@@ -24,6 +24,7 @@ MVP_ERR_TIMEOUT = -5
 MVP_ERR_DEVICE = -6
 
 MVP_F32, MVP_BF16, MVP_F16 = 0, 1, 2
+MVP_BLEND_SEQUENTIAL = 1
 
 
 class mvp_prims(ctypes.Structure):
@@ -34,7 +35,7 @@ class mvp_prims(ctypes.Structure):
 class mvp_rays(ctypes.Structure):
     _fields_ = [("n", c_int64), ("o", c_void_p), ("d", c_void_p), ("t_near", c_float), ("t_far", c_float),
                 ("dt", c_float), ("eps_early", c_float), ("bg", c_float * 3), ("width", c_int32),
-                ("height", c_int32)]
+                ("height", c_int32), ("flags", c_int32)]
 
 
 class mvp_request(ctypes.Structure):

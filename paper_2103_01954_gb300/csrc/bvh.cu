@@ -519,8 +519,9 @@ __device__ __forceinline__ void write_internal(Node *__restrict__ nodes, int i, 
   nodes[i] = N;
 }
 
-// One thread per node: leaf i (node n-1+i) and internal node i with the sorted leaf
-// range [first, last] it covers (range[i]). Blocks of 1024 also union their leaves'
+// One thread per node: leaf i (node n-1+i), the leaf position of its primitive
+// (rank), and internal node i with the sorted leaf range [first, last] it covers
+// (range[i]). Blocks of 1024 also union their leaves'
 // boxes in chunks of 32 (chunk1, one per warp) and 1024 (chunk2, one per block) for
 // the range refit.
 constexpr int HIER_THREADS = 1024;
@@ -528,7 +529,7 @@ __global__ void __launch_bounds__(HIER_THREADS) k_hierarchy(const uint32_t *__re
                                                             const int *__restrict__ kv, int n,
                                                             const float4 *__restrict__ pbox, Node *__restrict__ nodes,
                                                             int2 *__restrict__ range, float4 *__restrict__ chunk1,
-                                                            float4 *__restrict__ chunk2) {
+                                                            float4 *__restrict__ chunk2, int *__restrict__ rank) {
   __shared__ float sc[32][6];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i = blockIdx.x * HIER_THREADS + tid;
@@ -536,6 +537,7 @@ __global__ void __launch_bounds__(HIER_THREADS) k_hierarchy(const uint32_t *__re
   if (i < n) {
     const int k = kv[i];
     write_leaf(nodes, n, i, k, pbox);  // leaf i: node n-1+i
+    rank[k] = i;
     const float4 lo = pbox[2 * k], hi = pbox[2 * k + 1];
     b[0] = lo.x; b[1] = lo.y; b[2] = lo.z; b[3] = hi.x; b[4] = hi.y; b[5] = hi.z;
   }
@@ -659,6 +661,7 @@ cudaError_t bvh_reserve(BvhBuffers &b, int n) {
   size_t o_nodes = off; off = align_up(off + (size_t)(2 * cap) * sizeof(Node));
   size_t o_par = off; off = align_up(off + (size_t)(2 * cap) * sizeof(int));
   size_t o_gmc = off; off = align_up(off + (size_t)cap * 12 * sizeof(float));
+  size_t o_rank = off; off = align_up(off + (size_t)cap * sizeof(int));
   char *p = nullptr;
   cudaError_t e = cudaMalloc(&p, off);
   if (e != cudaSuccess) return e;
@@ -677,6 +680,7 @@ cudaError_t bvh_reserve(BvhBuffers &b, int n) {
   b.nodes = reinterpret_cast<Node *>(p + o_nodes);
   b.parent = reinterpret_cast<int *>(p + o_par);
   b.gmc = reinterpret_cast<float *>(p + o_gmc);
+  b.rank = reinterpret_cast<int *>(p + o_rank);
   return cudaSuccess;
 }
 
@@ -724,7 +728,7 @@ cudaError_t bvh_build(BvhBuffers &b, const float *t, const float *q, const float
   int2 *range = reinterpret_cast<int2 *>(b.parent);
   float4 *chunk1 = reinterpret_cast<float4 *>(b.keys_b), *chunk2 = reinterpret_cast<float4 *>(b.vals_b);
   k_hierarchy<<<(n + HIER_THREADS - 1) / HIER_THREADS, HIER_THREADS, 0, st>>>(b.keys_a, b.vals_a, n, b.pbox, b.nodes,
-                                                                              range, chunk1, chunk2);
+                                                                              range, chunk1, chunk2, b.rank);
   if (n > 1)
     k_refit_ranges<<<(n - 1 + REFIT_WARPS - 1) / REFIT_WARPS, REFIT_WARPS * 32, 0, st>>>(b.nodes, range, chunk1,
                                                                                           chunk2, n);

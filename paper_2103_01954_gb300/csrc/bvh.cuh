@@ -23,6 +23,7 @@ struct BvhBuffers {
   int *counts = nullptr;   // radix digit counts [256][blocks]
   Node *nodes = nullptr;   // [2n-1]
   int *parent = nullptr;   // [2n]: the internal nodes' sorted leaf ranges (int2) during the build
+  int *rank = nullptr;     // [n] each primitive's leaf position (its place in BVH order)
   float *gmc = nullptr;    // [n][12] adjoint accumulators of the march transform
 };
 

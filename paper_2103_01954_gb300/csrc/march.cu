@@ -4,7 +4,7 @@
 
 namespace mvp {
 
-template <int DT, int CAP, bool COUNT, int MT>
+template <int DT, int CAP, bool COUNT, int MT, bool SEQ = false>
 __global__ void __launch_bounds__(TILE_WARPS * 32, MVP_MARCH_MINB) k_march(MarchArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -14,7 +14,7 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, MVP_MARCH_MINB) k_march(March
   LaneRay L;
   load_lane_ray(L, a.o, a.d, tile_ray(a.geom, wt, lane));
   if (__ballot_sync(FULL, L.r >= 0) == 0) return;
-  march_tile<DT, CAP, COUNT, MT>(sh, a, L);
+  march_tile<DT, CAP, COUNT, MT, SEQ>(sh, a, L);
 }
 
 // ----------------------------------------------------------------------------
@@ -126,24 +126,29 @@ __global__ void __launch_bounds__(1024) k_offsets(const int64_t *__restrict__ co
 }
 
 // ----------------------------------------------------------------------------
-template <int DT, int CAP, bool COUNT, int MT>
+template <int DT, int CAP, bool COUNT, int MT, bool SEQ = false>
 static cudaError_t launch_march_t(const MarchArgs &a, cudaStream_t st) {
   size_t smem = sizeof(TileShared<CAP>) * TILE_WARPS;
   static bool attr_set = false;  // per instantiation; set once per process
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_march<DT, CAP, COUNT, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_march<DT, CAP, COUNT, MT, SEQ>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   int64_t blocks = (a.geom.n_warp_tiles + TILE_WARPS - 1) / TILE_WARPS;
   if (blocks == 0) return cudaSuccess;
-  k_march<DT, CAP, COUNT, MT><<<(unsigned)blocks, TILE_WARPS * 32, smem, st>>>(a);
+  k_march<DT, CAP, COUNT, MT, SEQ><<<(unsigned)blocks, TILE_WARPS * 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
 template <int DT, bool COUNT>
 static cudaError_t launch_march_m(const MarchArgs &a, cudaStream_t st) {
+  // paper-literal blending of saturating samples: the paper's voxel size and a generic-M
+  // kernel per payload type (evaluation counts do not depend on the blending rule)
+  if (!COUNT && a.sequential)
+    return a.M == 16 ? launch_march_t<DT, MARCH_CAP, false, 16, true>(a, st)
+                     : launch_march_t<DT, MARCH_CAP, false, 0, true>(a, st);
   switch (a.M) {
     case 8: return launch_march_t<DT, MARCH_CAP, COUNT, 8>(a, st);
     case 16: return launch_march_t<DT, MARCH_CAP, COUNT, 16>(a, st);

@@ -21,6 +21,8 @@ struct MarchArgs {
   const Node *nodes;
   const Pose *pose;
   const Xform *xf;
+  const int *rank;  // leaf position of each primitive (BVH order)
+  int sequential;   // blend a ray's saturating sample in BVH order (MVP_BLEND_SEQUENTIAL)
   // rays
   TileGeom geom;
   const float *o, *d;

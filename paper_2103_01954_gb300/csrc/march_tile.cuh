@@ -103,10 +103,55 @@ __device__ __forceinline__ bool sample_all(SH &sh, const MarchArgs &a, const Lan
   return ok;
 }
 
+// BVH order of a window list: sh.cand[p] = the entry of the p-th lowest leaf rank
+// (ranks are unique). The traversal buffers are free once the list is built; ranks go
+// to sh.stack, then each lane places the entries it holds by counting lower ranks.
+template <int CAP>
+__device__ __forceinline__ void order_window(TileShared<CAP> &sh, int ne, const int *__restrict__ rank) {
+  const int lane = threadIdx.x & 31;
+  static_assert(CAP <= 64 && CAP <= CBUF && CAP <= STACK, "window order buffers");
+  __syncwarp();
+  for (int e = lane; e < ne; e += 32) sh.stack[e] = __ldg(rank + sh.ek[e]);
+  __syncwarp();
+  for (int e = lane; e < ne; e += 32) {
+    const int rk = sh.stack[e];
+    int pos = 0;
+    for (int f = 0; f < ne; ++f) pos += sh.stack[f] < rk;
+    sh.cand[pos] = e;
+  }
+  __syncwarp();
+}
+
+// A lane's saturating sample ii (its summed opacity exceeds 1 - T) blended the
+// paper's way: the window's primitives that contain it, one by one in BVH order
+// (sh.cand, from order_window), each adding w = min(alpha dt, 1 - T) of its colour,
+// until T = 1. x is the sample's world position.
+template <int DT, int MT, int CAP>
+__device__ __forceinline__ void blend_sequential(const TileShared<CAP> &sh, int ne, const MarchArgs &a,
+                                                 const float x[3], int ii, int M, float Mm1, float &T, float &Ir,
+                                                 float &Ig, float &Ib) {
+  const int lane = threadIdx.x & 31;
+  float rem = 1.0f - T;
+  for (int p = 0; p < ne && rem > 0.0f; ++p) {
+    const int e = sh.cand[p];
+    const uint32_t r = sh.erng[e][lane];
+    if ((int)(r & 0xffffu) > ii || (int)(r >> 16) < ii) continue;
+    const float4 v = sample_rgba<DT, MT>(sh.exf[e], sh.eptr[e], x, M, Mm1);
+    const float w = fminf(v.w * a.dt, rem);
+    Ir = fmaf(v.x, w, Ir);
+    Ig = fmaf(v.y, w, Ig);
+    Ib = fmaf(v.z, w, Ib);
+    rem -= w;
+  }
+  T = 1.0f;
+}
+
 // March one warp tile whose lane ray is L (L.r < 0: no ray). Writes the output
 // (and the adjoint state / evaluation count) of each lane's ray. A traversal stack
 // overflow sets STATUS_CAPACITY in a.status; any number of primitives may overlap.
-template <int DT, int CAP, bool COUNT, int MT>
+// SEQ blends each ray's saturating sample in BVH order (within a window list; a
+// sample met by more primitives than a list holds keeps the summed rule).
+template <int DT, int CAP, bool COUNT, int MT, bool SEQ = false>
 __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs &a, const LaneRay &L) {
   const int lane = threadIdx.x & 31;
   const bool valid = L.r >= 0;
@@ -166,6 +211,7 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
       stack_full = true;
       break;
     }
+    if (SEQ && ne > 0) order_window<CAP>(sh, ne, a.rank);
     if (ne == WINDOW_FULL && w1 - w0 > 1) {  // split the depth range
       wlen = (w1 - w0 + 1) >> 1;
       continue;
@@ -268,12 +314,28 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
           if (COUNT) ++ne_c[c];
         }
       }
+      int seq_ii = -1;  // SEQ: the lane's saturating sample in this chunk
 #pragma unroll
       for (int c = 0; c < MARCH_CHUNK; ++c) {
         const int ii = i + c;
         if (!alive || ii >= ie) continue;
         if (COUNT) n_eval += ne_c[c];  // samples past a ray's termination are not counted
+        if (SEQ && sba[c].y * a.dt > 1.0f - T) {
+          seq_ii = ii;
+          alive = false;
+          continue;
+        }
         composite(srg[c], sba[c], ii);
+      }
+      if (SEQ && seq_ii >= 0) {  // blend the saturating sample in BVH order
+        const float ti = sample_t(a.t_near, a.dt, seq_ii);
+        const float xq[3] = {fmaf(ti, L.d[0], L.o[0]), fmaf(ti, L.d[1], L.o[1]), fmaf(ti, L.d[2], L.o[2])};
+        blend_sequential<DT, MT, CAP>(sh, ne, a, xq, seq_ii, M, Mm1, T, Ir, Ig, Ib);
+        if (a.saved) {
+          Saved S = {0.0f, 0.0f, 0.0f, 0.0f, seq_ii, -1};
+          a.saved[L.r] = S;
+        }
+        saved_done = true;
       }
       i = ie;
     }

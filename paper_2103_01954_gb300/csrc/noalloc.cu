@@ -42,7 +42,8 @@ constexpr size_t kOffValsB = align256(kOffValsA + (size_t)kMaxPrims * sizeof(int
 constexpr size_t kOffCounts = align256(kOffValsB + (size_t)kMaxPrims * sizeof(int));
 constexpr size_t kOffNodes = align256(kOffCounts + (size_t)256 * kMaxSortBlocks * sizeof(int));
 constexpr size_t kOffParent = align256(kOffNodes + (size_t)2 * kMaxPrims * sizeof(mvp::Node));
-constexpr size_t kBytes = align256(kOffParent + (size_t)2 * kMaxPrims * sizeof(int));
+constexpr size_t kOffRank = align256(kOffParent + (size_t)2 * kMaxPrims * sizeof(int));
+constexpr size_t kBytes = align256(kOffRank + (size_t)kMaxPrims * sizeof(int));
 
 static __device__ __align__(256) unsigned char g_static_scratch[kBytes];
 
@@ -74,7 +75,8 @@ extern "C" mvp_status mvp_raymarch_fwd_static(const mvp_prims *prims, const mvp_
     return reject(MVP_ERR_INVALID_ARG, "rays.n < 0 or a NULL ray/output array");
   if (reinterpret_cast<uintptr_t>(out_rgba) % 16) return reject(MVP_ERR_INVALID_ARG, "out_rgba is misaligned");
   if (!(rays->dt > 0.0f) || !(rays->t_far > rays->t_near) || !(rays->eps_early >= 0.0f && rays->eps_early < 1.0f) ||
-      !isfinite(rays->t_near) || !isfinite(rays->t_far) || !isfinite(rays->dt) || rays->width < 0 || rays->height < 0)
+      !isfinite(rays->t_near) || !isfinite(rays->t_far) || !isfinite(rays->dt) || rays->width < 0 || rays->height < 0 ||
+      (rays->flags & ~MVP_BLEND_SEQUENTIAL))
     return reject(MVP_ERR_INVALID_ARG, "bad ray parameters");
   const int64_t ns = mvp_num_steps(rays->t_near, rays->t_far, rays->dt);
   if (ns > MVP_MAX_STEPS) return reject(MVP_ERR_INVALID_ARG, "n_steps exceeds MVP_MAX_STEPS");
@@ -112,6 +114,7 @@ extern "C" mvp_status mvp_raymarch_fwd_static(const mvp_prims *prims, const mvp_
   b.counts = reinterpret_cast<int *>(base + kOffCounts);
   b.nodes = reinterpret_cast<mvp::Node *>(base + kOffNodes);
   b.parent = reinterpret_cast<int *>(base + kOffParent);
+  b.rank = reinterpret_cast<int *>(base + kOffRank);
   cudaError_t e = mvp::bvh_build(b, prims->t, prims->q, prims->s, prims->n, prims->M, st);
   if (e != cudaSuccess) return reject(MVP_ERR_CUDA, "BVH build launch failed");
 
@@ -125,6 +128,8 @@ extern "C" mvp_status mvp_raymarch_fwd_static(const mvp_prims *prims, const mvp_
     a.nodes = b.nodes;
     a.pose = b.pose;
     a.xf = b.xf;
+    a.rank = b.rank;
+    a.sequential = (rays->flags & MVP_BLEND_SEQUENTIAL) ? 1 : 0;
     a.geom = mvp::make_tile_geom(rays->n, rays->width, rays->height);
     a.o = rays->o;
     a.d = rays->d;
