@@ -234,6 +234,14 @@ typedef struct mvp_request {
                           * is then [2][height][width][4], view 0 from c2w, view 1 from
                           * c2w_right */
   float c2w_right[12];   /* second view's camera (views = 2) */
+  const void *payload;   /* NULL: the avatar's payload. Else this request's own payload
+                          * (device, caller-owned; the avatar's n, M and dtype and its
+                          * alignment), e.g. the view-dependent payload assembled for
+                          * this camera by mvp_assemble_payload; both views of a stereo
+                          * request use it. Its writes must be complete before the call
+                          * (synchronise the producing stream), and it must stay valid
+                          * until the request completes. It does not count against the
+                          * server's HBM budget. */
 } mvp_request;
 
 typedef struct mvp_serve_info {
@@ -288,6 +296,16 @@ MVP_API mvp_status mvp_serve_stats(mvp_server *server, mvp_serve_info *info);
  * place) it gives the gradient with respect to the unfaded opacity. */
 MVP_API mvp_status mvp_fade_payload(mvp_ctx *ctx, const float *src, void *dst, int64_t n_prims, int32_t M,
                                     int32_t dtype, float alpha, int32_t beta, mvp_stream stream);
+/* A view's payload (Sec. 3.1.3: the colour decoder takes a view vector, the opacity
+ * decoder does not): dst voxel = (rgb, opacity x W) with W the opacity fade above
+ * (alpha = 0 gives W = 1). rgb [n_prims][M][M][M][3] FP32 (the view-dependent colour
+ * decoded for this view), opacity [n_prims][M][M][M] FP32 (shared by every view), both
+ * device, 4-byte aligned; dst [n_prims][M][M][M][4] in `dtype` (FP32, BF16 or FP16,
+ * round to nearest even), 16-byte (FP32) or 8-byte aligned, overlapping neither input.
+ * The result feeds mvp_prims.payload, or mvp_request.payload for one serving request. */
+MVP_API mvp_status mvp_assemble_payload(mvp_ctx *ctx, const float *rgb, const float *opacity, void *dst,
+                                        int64_t n_prims, int32_t M, int32_t dtype, float alpha, int32_t beta,
+                                        mvp_stream stream);
 /* Rotation from an axis-angle (Rodrigues) vector (Sec. 3.1.2: the paper's rotation
  * parameterisation): q = (cos(th/2), sin(th/2) r/th), th = |r| (q = (1, 0, 0, 0) at
  * r = 0). r [n][3], q [n][4] FP32 device; q feeds mvp_prims.q. */

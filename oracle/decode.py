@@ -5,6 +5,8 @@ TEST INFRASTRUCTURE: the oracle is never on the product path. Plain numpy, writt
 from the paper's definitions:
 - opacity fade factor (Sec. 3.1.3, Eq. for W): W(x, y, z) = exp(-alpha (x^beta + y^beta
   + z^beta)) over normalised payload coordinates in [-1, 1]^3, multiplying opacity;
+- a view's payload (Sec. 3.1.3): RGB from the view-conditioned colour decoder, opacity
+  from the view-independent one, faded, interleaved as RGBA;
 - rotation from an axis-angle (Rodrigues) vector (Sec. 3.1.2), as a unit quaternion;
 - volume minimisation prior (Sec. 3.3): L_vol = lambda sum_i Prod(s_i) over the
   primitives' side lengths.
@@ -27,6 +29,17 @@ def fade_payload(payload, alpha: float = 8.0, beta: int = 8) -> np.ndarray:
     """payload [n][M][M][M][4] with the opacity (channel 3) multiplied by W (FP64)."""
     P = np.array(payload, dtype=np.float64)
     P[..., 3] *= fade_window(P.shape[1], alpha, beta)[None]
+    return P
+
+
+def assemble_payload(rgb, opacity, alpha: float = 8.0, beta: int = 8) -> np.ndarray:
+    """[n][M][M][M][4] FP64: channels 0-2 the view's colour rgb [n][M][M][M][3],
+    channel 3 the shared opacity [n][M][M][M] times W (no fade at alpha = 0)."""
+    rgb = np.asarray(rgb, np.float64)
+    op = np.asarray(opacity, np.float64)
+    P = np.empty(rgb.shape[:-1] + (4,))
+    P[..., :3] = rgb
+    P[..., 3] = op * fade_window(rgb.shape[1], alpha, beta)[None]
     return P
 
 

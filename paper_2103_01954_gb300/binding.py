@@ -41,7 +41,8 @@ class mvp_rays(ctypes.Structure):
 class mvp_request(ctypes.Structure):
     _fields_ = [("avatar", c_int32), ("width", c_int32), ("height", c_int32), ("focal", c_float),
                 ("c2w", c_float * 12), ("t_near", c_float), ("t_far", c_float), ("dt", c_float),
-                ("eps_early", c_float), ("bg", c_float * 3), ("views", c_int32), ("c2w_right", c_float * 12)]
+                ("eps_early", c_float), ("bg", c_float * 3), ("views", c_int32), ("c2w_right", c_float * 12),
+                ("payload", c_void_p)]
 
 
 class mvp_serve_info(ctypes.Structure):
@@ -96,6 +97,8 @@ _SIGS = [
                                           c_void_p]),
     ("mvp_fade_payload", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_float, c_int32,
                                    c_void_p]),
+    ("mvp_assemble_payload", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_float,
+                                       c_int32, c_void_p]),
     ("mvp_axis_angle_to_quat", c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     ("mvp_axis_angle_backward", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     ("mvp_volume_prior", c_int32, [c_void_p, c_void_p, c_int32, c_float, c_void_p, c_void_p, c_void_p]),

@@ -428,6 +428,31 @@ mvp_status mvp_fade_payload(mvp_ctx *ctx, const float *src, void *dst, int64_t n
   return ok();
 }
 
+mvp_status mvp_assemble_payload(mvp_ctx *ctx, const float *rgb, const float *opacity, void *dst, int64_t n_prims,
+                                int32_t M, int32_t dtype, float alpha, int32_t beta, mvp_stream stream) {
+  if (!ctx) return fail(MVP_ERR_INVALID_ARG, "ctx is NULL");
+  if (n_prims < 0 || n_prims > MVP_MAX_PRIMS) return fail(MVP_ERR_INVALID_ARG, "n_prims out of range");
+  if (M < 2 || M > MVP_MAX_M) return fail(MVP_ERR_INVALID_ARG, "M out of [2, %d]", MVP_MAX_M);
+  if (dtype != MVP_F32 && dtype != MVP_BF16 && dtype != MVP_F16) return fail(MVP_ERR_INVALID_ARG, "dtype unknown");
+  if (!finite(alpha) || beta < 0 || beta > 64) return fail(MVP_ERR_INVALID_ARG, "alpha not finite or beta out of [0, 64]");
+  if (n_prims > 0 && (!rgb || !opacity || !dst)) return fail(MVP_ERR_INVALID_ARG, "NULL buffer");
+  if (reinterpret_cast<uintptr_t>(rgb) % 4 || reinterpret_cast<uintptr_t>(opacity) % 4 ||
+      reinterpret_cast<uintptr_t>(dst) % (dtype == MVP_F32 ? 16 : 8))
+    return fail(MVP_ERR_INVALID_ARG, "misaligned buffer");
+  if (n_prims > 0) {
+    const size_t nv = (size_t)n_prims * M * M * M;
+    const char *o = reinterpret_cast<const char *>(dst);
+    const size_t ob = nv * (dtype == MVP_F32 ? 16 : 8);
+    const char *c = reinterpret_cast<const char *>(rgb), *a = reinterpret_cast<const char *>(opacity);
+    if ((c < o + ob && o < c + nv * 12) || (a < o + ob && o < a + nv * 4))
+      return fail(MVP_ERR_INVALID_ARG, "dst overlaps an input");
+  }
+  DeviceGuard g(ctx->device);
+  cudaError_t e = mvp::launch_assemble(rgb, opacity, dst, n_prims, M, dtype, alpha, beta, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "assemble launch");
+  return ok();
+}
+
 mvp_status mvp_axis_angle_to_quat(mvp_ctx *ctx, const float *r, int32_t n, float *q, mvp_stream stream) {
   if (!ctx) return fail(MVP_ERR_INVALID_ARG, "ctx is NULL");
   if (n < 0) return fail(MVP_ERR_INVALID_ARG, "n < 0");

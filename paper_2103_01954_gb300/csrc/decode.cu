@@ -1,7 +1,8 @@
 // decode.cu -- the steps just upstream of the march that turn decoder output into
-// march inputs, and their gradients: the opacity fade factor (Sec. 3.1.3), rotations
-// from axis-angle (Rodrigues) vectors (Sec. 3.1.2), and the volume minimisation prior
-// (Sec. 3.3).
+// march inputs, and their gradients: the opacity fade factor (Sec. 3.1.3), the
+// assembly of a view's payload from view-dependent colour and opacity (Sec. 3.1.3),
+// rotations from axis-angle (Rodrigues) vectors (Sec. 3.1.2), and the volume
+// minimisation prior (Sec. 3.3).
 #include "pack.cuh"
 
 namespace mvp {
@@ -19,6 +20,34 @@ __device__ __forceinline__ float ipow(float x, int b) {
   return r;
 }
 
+// W at voxel position v of an M^3 grid.
+__device__ __forceinline__ float fade_weight(int v, int M, float alpha, int beta) {
+  const int x = v % M, y = (v / M) % M, z = v / (M * M);
+  const float h = 2.0f / (float)(M - 1);
+  const float fx = fmaf((float)x, h, -1.0f), fy = fmaf((float)y, h, -1.0f), fz = fmaf((float)z, h, -1.0f);
+  return expf(-alpha * (ipow(fx, beta) + ipow(fy, beta) + ipow(fz, beta)));
+}
+
+// Voxel i of a payload in type DT (round to nearest even).
+template <int DT>
+__device__ __forceinline__ void store_voxel(void *dst, int64_t i, float4 c) {
+  if (DT == MVP_F32) {
+    reinterpret_cast<float4 *>(dst)[i] = c;
+  } else if (DT == MVP_BF16) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(c.x, c.y), b = __floats2bfloat162_rn(c.z, c.w);
+    uint2 o;
+    o.x = *reinterpret_cast<uint32_t *>(&a);
+    o.y = *reinterpret_cast<uint32_t *>(&b);
+    reinterpret_cast<uint2 *>(dst)[i] = o;
+  } else {
+    __half2 a = __floats2half2_rn(c.x, c.y), b = __floats2half2_rn(c.z, c.w);
+    uint2 o;
+    o.x = *reinterpret_cast<uint32_t *>(&a);
+    o.y = *reinterpret_cast<uint32_t *>(&b);
+    reinterpret_cast<uint2 *>(dst)[i] = o;
+  }
+}
+
 // One thread per voxel position v of the M^3 grid (blockIdx.x) computes W once and
 // applies it to voxel v of primitives blockIdx.y, blockIdx.y + gridDim.y, ... src and
 // dst may be the same buffer (dst FP32): each element is read, then written, by one
@@ -29,29 +58,29 @@ __global__ void __launch_bounds__(256) k_fade(const float4 *src, void *dst, int6
   const int M3 = M * M * M;
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= M3) return;
-  const int x = v % M, y = (v / M) % M, z = v / (M * M);
-  const float h = 2.0f / (float)(M - 1);
-  const float fx = fmaf((float)x, h, -1.0f), fy = fmaf((float)y, h, -1.0f), fz = fmaf((float)z, h, -1.0f);
-  const float w = expf(-alpha * (ipow(fx, beta) + ipow(fy, beta) + ipow(fz, beta)));
+  const float w = fade_weight(v, M, alpha, beta);
   for (int64_t k = blockIdx.y; k < n_prims; k += gridDim.y) {
     const int64_t i = k * M3 + v;
     float4 c = src[i];
     c.w *= w;
-    if (DT == MVP_F32) {
-      reinterpret_cast<float4 *>(dst)[i] = c;
-    } else if (DT == MVP_BF16) {
-      __nv_bfloat162 a = __floats2bfloat162_rn(c.x, c.y), b = __floats2bfloat162_rn(c.z, c.w);
-      uint2 o;
-      o.x = *reinterpret_cast<uint32_t *>(&a);
-      o.y = *reinterpret_cast<uint32_t *>(&b);
-      reinterpret_cast<uint2 *>(dst)[i] = o;
-    } else {
-      __half2 a = __floats2half2_rn(c.x, c.y), b = __floats2half2_rn(c.z, c.w);
-      uint2 o;
-      o.x = *reinterpret_cast<uint32_t *>(&a);
-      o.y = *reinterpret_cast<uint32_t *>(&b);
-      reinterpret_cast<uint2 *>(dst)[i] = o;
-    }
+    store_voxel<DT>(dst, i, c);
+  }
+}
+
+// A view's payload: voxel i = (rgb[i], alpha[i] W) from the view-dependent colour
+// [n][M^3][3] and the view-independent opacity [n][M^3], same grid as k_fade.
+template <int DT>
+__global__ void __launch_bounds__(256) k_assemble(const float *__restrict__ rgb, const float *__restrict__ op,
+                                                  void *__restrict__ dst, int64_t n_prims, int M, float alpha,
+                                                  int beta) {
+  const int M3 = M * M * M;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= M3) return;
+  const float w = fade_weight(v, M, alpha, beta);
+  for (int64_t k = blockIdx.y; k < n_prims; k += gridDim.y) {
+    const int64_t i = k * M3 + v;
+    const float4 c = make_float4(__ldg(rgb + 3 * i), __ldg(rgb + 3 * i + 1), __ldg(rgb + 3 * i + 2), __ldg(op + i) * w);
+    store_voxel<DT>(dst, i, c);
   }
 }
 
@@ -126,18 +155,33 @@ __global__ void __launch_bounds__(256) k_volume_prior(const float *__restrict__ 
   }
 }
 
+// Voxel-position blocks in x; enough blocks in y to fill the GPU several times over,
+// each looping over primitives.
+static dim3 voxel_grid(int64_t n_prims, int M) {
+  const int M3 = M * M * M;
+  const unsigned gx = (unsigned)((M3 + 255) / 256);
+  const int64_t want = (4 * 152 * 8 + gx - 1) / gx;
+  return dim3(gx, (unsigned)(n_prims < want ? n_prims : (want > 65535 ? 65535 : want)));
+}
+
 cudaError_t launch_fade(const float *src, void *dst, int64_t n_prims, int M, int dtype, float alpha, int beta,
                         cudaStream_t st) {
   if (n_prims <= 0) return cudaSuccess;
-  const int M3 = M * M * M;
-  // enough blocks in y to fill the GPU several times over, each looping over primitives
-  const unsigned gx = (unsigned)((M3 + 255) / 256);
-  const int64_t want = (4 * 152 * 8 + gx - 1) / gx;
-  const dim3 grid(gx, (unsigned)(n_prims < want ? n_prims : (want > 65535 ? 65535 : want)));
+  const dim3 grid = voxel_grid(n_prims, M);
   const float4 *s4 = reinterpret_cast<const float4 *>(src);
   if (dtype == MVP_F32) k_fade<MVP_F32><<<grid, 256, 0, st>>>(s4, dst, n_prims, M, alpha, beta);
   else if (dtype == MVP_BF16) k_fade<MVP_BF16><<<grid, 256, 0, st>>>(s4, dst, n_prims, M, alpha, beta);
   else k_fade<MVP_F16><<<grid, 256, 0, st>>>(s4, dst, n_prims, M, alpha, beta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(const float *rgb, const float *op, void *dst, int64_t n_prims, int M, int dtype,
+                            float alpha, int beta, cudaStream_t st) {
+  if (n_prims <= 0) return cudaSuccess;
+  const dim3 grid = voxel_grid(n_prims, M);
+  if (dtype == MVP_F32) k_assemble<MVP_F32><<<grid, 256, 0, st>>>(rgb, op, dst, n_prims, M, alpha, beta);
+  else if (dtype == MVP_BF16) k_assemble<MVP_BF16><<<grid, 256, 0, st>>>(rgb, op, dst, n_prims, M, alpha, beta);
+  else k_assemble<MVP_F16><<<grid, 256, 0, st>>>(rgb, op, dst, n_prims, M, alpha, beta);
   return cudaGetLastError();
 }
 

@@ -241,7 +241,7 @@ mvp_status launch(mvp_server *S, InFlight &f) {
   m.n_prims = A.prims.n;
   m.M = A.prims.M;
   m.dtype = A.prims.dtype;
-  m.payload = A.prims.payload;
+  m.payload = q.payload ? q.payload : A.prims.payload;  // a request's own (view-dependent) payload
   m.nodes = A.bvh.nodes;
   m.pose = A.bvh.pose;
   m.xf = A.bvh.xf;
@@ -436,6 +436,9 @@ mvp_status mvp_serve_submit(mvp_server *S, const mvp_request *req, uint64_t *tic
   for (int i = 0; i < 12; ++i)
     if (!isfinite(req->c2w[i]) || (req->views == 2 && !isfinite(req->c2w_right[i])))
       return serve_fail(MVP_ERR_INVALID_ARG, "camera must be finite");
+  if (req->payload &&
+      reinterpret_cast<uintptr_t>(req->payload) % (S->avatars[req->avatar].prims.dtype == MVP_F32 ? 16 : 8))
+    return serve_fail(MVP_ERR_INVALID_ARG, "request payload misaligned");
   const size_t bytes = image_bytes(*req);
   if (S->resident + bytes > S->budget || ((bytes + 255) & ~size_t(255)) > S->arena.size)
     return serve_fail(MVP_ERR_CAPACITY, "request image exceeds the HBM budget");

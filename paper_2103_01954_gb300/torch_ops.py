@@ -192,6 +192,23 @@ def fade_payload(ctx: Context, payload_f32: torch.Tensor, dtype: torch.dtype = t
     return out
 
 
+def assemble_payload(ctx: Context, rgb: torch.Tensor, opacity: torch.Tensor, dtype: torch.dtype = torch.bfloat16,
+                     alpha: float = 8.0, beta: int = 8, out: torch.Tensor | None = None) -> torch.Tensor:
+    """mvp_assemble_payload: a view's payload [n, M, M, M, 4] in `dtype` from its
+    view-dependent colour rgb [n, M, M, M, 3] and the shared opacity [n, M, M, M]
+    (faded with alpha, beta; alpha = 0: no fade)."""
+    _need(rgb, "rgb", torch.float32, (3,))
+    _need(opacity, "opacity", torch.float32)
+    n, M = rgb.shape[0], rgb.shape[1]
+    if tuple(opacity.shape) != tuple(rgb.shape[:-1]):
+        raise ValueError("opacity must be rgb's shape without the channel axis")
+    if out is None:
+        out = torch.empty((n, M, M, M, 4), dtype=dtype, device=rgb.device)
+    B.check(B.lib().mvp_assemble_payload(ctx.handle, _ptr(rgb), _ptr(opacity), _ptr(out), n, M, _DT[dtype],
+                                         float(alpha), int(beta), _stream()), "mvp_assemble_payload")
+    return out
+
+
 def axis_angle_to_quat(ctx: Context, r: torch.Tensor) -> torch.Tensor:
     _need(r, "r", torch.float32, (3,))
     q = torch.empty((r.shape[0], 4), dtype=torch.float32, device=r.device)
@@ -290,10 +307,14 @@ class Server:
 
     @staticmethod
     def request(avatar: int, c2w, focal: float, width: int, height: int, t_near: float, t_far: float, dt: float,
-                eps_early: float = 0.0, bg=(0.0, 0.0, 0.0), c2w_right=None) -> B.mvp_request:
-        """A request; with c2w_right, a stereo pair whose image is [2][height][width][4]."""
+                eps_early: float = 0.0, bg=(0.0, 0.0, 0.0), c2w_right=None, payload=None) -> B.mvp_request:
+        """A request; with c2w_right, a stereo pair whose image is [2][height][width][4];
+        with payload (a device tensor in the avatar's layout and dtype), the request
+        renders that payload instead of the avatar's (the caller keeps it alive until
+        the request completes)."""
         r = B.mvp_request(avatar=avatar, width=width, height=height, focal=focal, t_near=t_near, t_far=t_far, dt=dt,
-                          eps_early=eps_early, views=1 if c2w_right is None else 2)
+                          eps_early=eps_early, views=1 if c2w_right is None else 2,
+                          payload=None if payload is None else payload.data_ptr())
         for i, v in enumerate([float(x) for x in list(c2w.reshape(-1))]):
             r.c2w[i] = v
         if c2w_right is not None:

@@ -22,4 +22,5 @@ from .scenes import (  # noqa: F401
     make_scene,
     make_target,
     random_unit_quaternions,
+    view_colors,
 )

@@ -116,6 +116,23 @@ def make_payload(rng: np.random.Generator, n: int, M: int, empty_frac: float,
     return out
 
 
+def view_colors(scene: Scene, view, seed: int = 0, strength: float = 0.5, power: int = 8) -> np.ndarray:
+    """Stand-in for the view-conditioned colour decoder's output (the paper's colour
+    decoder takes an object-centric view vector; its weights are not available):
+    [N, M, M, M, 3] float32 = the scene's RGB plus a seeded per-voxel highlight
+    strength * max(0, n . v)^power, clipped to [0, 1], with n a seeded unit vector per
+    voxel (the same for every view) and v the unit view vector."""
+    v = np.asarray(view, np.float32)
+    v = v / np.linalg.norm(v)
+    rng = np.random.default_rng(1000 + seed)
+    shape = scene.payload.shape[:-1]
+    nrm = rng.standard_normal(shape + (3,), dtype=np.float32)
+    nrm /= np.linalg.norm(nrm, axis=-1, keepdims=True)
+    lobe = np.maximum(nrm @ v, 0.0) ** power
+    rgb = scene.payload[..., :3] + np.float32(strength) * lobe[..., None]
+    return np.clip(rgb, 0.0, 1.0).astype(np.float32)
+
+
 def make_scene(n: int, M: int, seed: int, layout: str = "shell",
                s_range=(0.04, 0.08), s_const: float | None = None,
                empty_frac: float = 0.6, fade: bool = False,

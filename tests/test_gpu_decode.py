@@ -72,6 +72,67 @@ def test_faded_payload_renders_like_the_oracle():
     assert st["frac_2e-4"] >= 0.999 and st["max"] <= 1e-2, st
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
+@pytest.mark.parametrize("M,n,alpha", [(8, 37, 8.0), (16, 5, 8.0), (3, 1000, 0.0), (32, 2, 2.0)])
+def test_assemble_matches_oracle(dtype, M, n, alpha):
+    """A view's payload from its colour and the shared opacity: colour channels are the
+    input rounded once to the stored type; opacity within the fade's FP32 bound."""
+    ctx = T.Context(0)
+    rng = np.random.default_rng(M * 10 + n)
+    rgb = rng.uniform(0.0, 1.0, (n, M, M, M, 3)).astype(np.float32)
+    op = rng.uniform(0.0, 4.0, (n, M, M, M)).astype(np.float32)
+    g = T.assemble_payload(ctx, torch.from_numpy(rgb).to(DEV), torch.from_numpy(op).to(DEV), dtype, alpha, 8)
+    ctx.sync()
+    got = g.float().cpu().numpy().astype(np.float64)
+    ref = D.assemble_payload(rgb, op, alpha, 8)
+    assert np.array_equal(got[..., :3], torch.from_numpy(rgb).to(dtype).double().numpy())
+    floor = 2.0 ** -25 if dtype == torch.float16 else 0.0
+    tol = (ULP[dtype] + alpha * 3 * 8 * 4 * ULP[torch.float32]) * np.abs(ref[..., 3]) + floor + 1e-30
+    assert np.all(np.abs(got[..., 3] - ref[..., 3]) <= tol)
+    if alpha == 0.0:  # no fade: the opacity is only rounded to the stored type
+        assert np.array_equal(got[..., 3], torch.from_numpy(op).to(dtype).double().numpy())
+
+
+def test_assemble_rejects_overlap_and_misalignment():
+    ctx = T.Context(0)
+    buf = torch.zeros(4 * 6 ** 3 * 4 + 8, device=DEV)
+    rgb = torch.rand((4, 6, 6, 6, 3), device=DEV)
+    op = torch.rand((4, 6, 6, 6), device=DEV)
+    lib = B.lib()
+    # destination over the colour input
+    st = lib.mvp_assemble_payload(ctx.handle, T._ptr(rgb), T._ptr(op), T._ptr(rgb), 4, 6, B.MVP_BF16, 8.0, 8, None)
+    assert st == B.MVP_ERR_INVALID_ARG
+    # FP32 destination not 16-byte aligned
+    st = lib.mvp_assemble_payload(ctx.handle, T._ptr(rgb), T._ptr(op), buf.data_ptr() + 4, 4, 6, B.MVP_F32, 8.0, 8,
+                                  None)
+    assert st == B.MVP_ERR_INVALID_ARG
+    st = lib.mvp_assemble_payload(ctx.handle, T._ptr(rgb), T._ptr(op), T._ptr(buf), 4, 6, B.MVP_F32, 8.0, 8, None)
+    assert st == B.MVP_OK
+    ctx.sync()
+
+
+def test_view_payloads_render_like_the_oracle():
+    """Two views' payloads assembled on the device (BF16, faded) render as the oracle
+    renders the same dequantised payloads, and the two views' images differ."""
+    sc, rays, _ = synthetic.make_config("small_512x8^3_96x128", 3)
+    ctx = T.Context(0)
+    op = torch.from_numpy(np.ascontiguousarray(sc.payload[..., 3])).to(DEV)
+    imgs = []
+    for view in ((0.0, 0.0, 1.0), (1.0, 0.0, 0.0)):
+        rgb = synthetic.view_colors(sc, view, seed=3)
+        pb = T.assemble_payload(ctx, torch.from_numpy(rgb).to(DEV), op, torch.bfloat16, 8.0, 8)
+        dv = Dev(sc, rays, ctx=ctx)
+        dv.payload = pb
+        dv.prims = T.prims_struct(dv.t, dv.q, dv.s, pb)
+        out, _ = dv.build().render()
+        deq = pb.float().cpu().numpy()
+        ref = oracle.render(synthetic.Scene(t=sc.t, q=sc.q, s=sc.s, payload=deq, M=sc.M), rays, F32M)["rgba"]
+        st = image_parity(out.cpu().numpy(), ref)
+        assert st["frac_2e-4"] >= 0.999 and st["max"] <= 1e-2, st
+        imgs.append(out.cpu().numpy())
+    assert np.abs(imgs[0] - imgs[1]).max() > 1e-2
+
+
 def test_axis_angle_and_gradient_match_oracle():
     ctx = T.Context(0)
     rng = np.random.default_rng(3)

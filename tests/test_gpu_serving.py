@@ -179,3 +179,43 @@ def test_stereo_request_equals_two_mono_requests():
         assert not torch.equal(both[0], both[1])  # the eyes see different images
     assert srv.stats()["device_status"] == 0
     srv.close()
+
+
+def test_request_payload_override():
+    """A request carrying its own (view-dependent) payload renders exactly what an avatar
+    registered with that payload renders, mono and stereo; a misaligned one is refused."""
+    torch.cuda.set_device(0)
+    ctx = T.Context(0)
+    av = _avatars(ctx)[1]  # BF16
+    t, q, s, p = av
+    n, M = p.shape[0], p.shape[1]
+    rgb = torch.rand((n, M, M, M, 3), device=DEV)
+    op = p[..., 3].float().contiguous()
+    pv = T.assemble_payload(ctx, rgb, op, torch.bfloat16, 0.0, 8)  # same opacity, another view's colour
+    ctx.sync()
+    srv = T.Server(ctx, hbm_budget=2 << 30, max_slots=8)
+    a_base = srv.register(t, q, s, p)
+    a_view = srv.register(t, q, s, pv)
+    w, h = 72, 56
+    cam = _cams(1, 5)[0]
+    right = cam.copy()
+    right[:, 3] += 0.064 * right[:, 0]
+    for c2 in (None, right):
+        nv = 1 if c2 is None else 2
+        imgs = []
+        for aid, payload in ((a_base, pv), (a_view, None), (a_base, None)):
+            tk = srv.submit_raw(T.Server.request(aid, cam, float(w), w, h, T_NEAR, T_FAR, DT, c2w_right=c2,
+                                                 payload=payload))
+            img = torch.empty((nv, h * w, 4), dtype=torch.float32, device=DEV)
+            st, _ = srv.wait(tk, 10000.0, img)
+            assert st == B.MVP_OK
+            imgs.append(img)
+        assert torch.equal(imgs[0], imgs[1])      # override == avatar registered with it
+        assert not torch.equal(imgs[0], imgs[2])  # and not the avatar's own payload
+    bad = T.Server.request(a_base, cam, float(w), w, h, T_NEAR, T_FAR, DT)
+    bad.payload = pv.data_ptr() + 4
+    with pytest.raises(B.MVPError) as ei:
+        srv.submit_raw(bad)
+    assert ei.value.status == B.MVP_ERR_INVALID_ARG
+    assert srv.stats()["device_status"] == 0
+    srv.close()

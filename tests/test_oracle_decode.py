@@ -72,3 +72,17 @@ def test_volume_prior_closed_form_and_gradient():
             sm[k, j] -= h
             fd = (D.volume_prior(sp, 0.01)[0] - D.volume_prior(sm, 0.01)[0]) / (2 * h)
             assert np.isclose(g[k, j], fd, rtol=1e-7)
+
+
+def test_assemble_payload_interleaves_and_fades():
+    rng = np.random.default_rng(3)
+    rgb = rng.uniform(0, 1, (2, 5, 5, 5, 3))
+    op = rng.uniform(0, 4, (2, 5, 5, 5))
+    P = D.assemble_payload(rgb, op, 0.0, 8)  # no fade: plain interleaving
+    assert P.shape == (2, 5, 5, 5, 4)
+    assert np.array_equal(P[..., :3], rgb) and np.array_equal(P[..., 3], op)
+    F = D.assemble_payload(rgb, op, 8.0, 8)
+    assert np.array_equal(F[..., :3], rgb)
+    assert F[0, 2, 2, 2, 3] == op[0, 2, 2, 2]                      # W = 1 at the centre
+    assert np.isclose(F[1, 0, 0, 0, 3], op[1, 0, 0, 0] * np.exp(-24.0))  # a corner
+    assert np.isclose(F[1, 2, 2, 4, 3], op[1, 2, 2, 4] * np.exp(-8.0))   # a face centre
