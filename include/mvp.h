@@ -129,8 +129,14 @@ MVP_API int64_t mvp_num_steps(float t_near, float t_far, float dt);
 MVP_API mvp_status mvp_ctx_create(int device, mvp_ctx **out);
 MVP_API void mvp_ctx_destroy(mvp_ctx *ctx);
 /* Synchronises `stream`, then reads and clears the device status word:
- * MVP_ERR_CAPACITY if a kernel hit a capacity limit since the last sync, else
- * MVP_OK (or MVP_ERR_CUDA if the stream reported an error). */
+ * MVP_ERR_CAPACITY if a kernel hit a capacity limit since the last sync
+ * (MVP_STATUS_CAPACITY), MVP_ERR_INVALID_ARG if a BVH build met a primitive whose
+ * pose defines no box (MVP_STATUS_POSE: t, q or s not finite, q = 0 or s <= 0;
+ * renders that used it are finite and read nothing out of bounds, but that
+ * primitive's contribution is unspecified), else MVP_OK (or MVP_ERR_CUDA if the
+ * stream reported an error). */
+#define MVP_STATUS_CAPACITY 1
+#define MVP_STATUS_POSE 4
 MVP_API mvp_status mvp_ctx_sync(mvp_ctx *ctx, mvp_stream stream);
 
 /* ------------------------------------------------------ BVH (Sec. 3.2.1) */
@@ -252,6 +258,7 @@ typedef struct mvp_serve_info {
   int32_t device_status;  /* status bits set by the serving kernel (0: none) */
   int32_t reserved;
   int64_t batches;        /* request launches so far */
+  int64_t cancelled;      /* requests cancelled so far */
 } mvp_serve_info;
 
 /* hbm_budget: bytes for resident avatars (payload + BVH) plus images in flight;
@@ -264,7 +271,8 @@ MVP_API mvp_status mvp_serve_create(mvp_ctx *ctx, size_t hbm_budget, int32_t max
 MVP_API void mvp_serve_destroy(mvp_server *server);
 /* Keeps `prims` (device pointers, caller-owned, must stay valid) resident and builds
  * its BVH once (avatars do not move between requests). Synchronises.
- * MVP_ERR_CAPACITY if it does not fit the budget. */
+ * MVP_ERR_CAPACITY if it does not fit the budget; MVP_ERR_INVALID_ARG if a
+ * primitive's pose defines no box (see MVP_STATUS_POSE). */
 MVP_API mvp_status mvp_serve_register_avatar(mvp_server *server, const mvp_prims *prims, int32_t *avatar_id);
 /* Queues a request and admits what fits; *ticket identifies it. MVP_ERR_CAPACITY
  * if the image alone exceeds the budget or the arena; MVP_ERR_INVALID_ARG for a
@@ -275,6 +283,11 @@ MVP_API mvp_status mvp_serve_submit(mvp_server *server, const mvp_request *req, 
  * pointer, or NULL to drop it) and releasing its slot and memory. latency_ms
  * (nullable) = host time from submit until this poll saw it done. */
 MVP_API mvp_status mvp_serve_poll(mvp_server *server, uint64_t ticket, float *out_rgba, double *latency_ms);
+/* Withdraws a request: a queued one is dropped before anything runs; a running one
+ * finishes on the device (its launch cannot be stopped) and the server frees its
+ * slot and image memory once it is done. Either way the ticket is unknown from now
+ * on. MVP_ERR_INVALID_ARG for an unknown (or already collected) ticket. */
+MVP_API mvp_status mvp_serve_cancel(mvp_server *server, uint64_t ticket);
 /* Polls until done or timeout_ms passes (MVP_ERR_TIMEOUT, request still queued or
  * running). */
 MVP_API mvp_status mvp_serve_wait(mvp_server *server, uint64_t ticket, double timeout_ms, float *out_rgba,
@@ -337,7 +350,8 @@ MVP_API mvp_status mvp_volume_prior(mvp_ctx *ctx, const float *s, int32_t n, flo
  * the same array and it keeps the last call's contents; calls whose GPU work
  * overlaps (other streams or threads) race on it and must be serialised by the
  * caller. status_out (device int32, nullable) receives the kernels' status bits
- * (1: more primitives overlapped one sample of a ray tile than a tile holds).
+ * (MVP_STATUS_CAPACITY: a tile's BVH traversal stack overflowed; MVP_STATUS_POSE: a
+ * primitive's pose defines no box).
  * Asynchronous on `stream`; no adjoint state is saved. */
 #define MVP_STATIC_MAX_PRIMS 16384
 MVP_API mvp_status mvp_raymarch_fwd_static(const mvp_prims *prims, const mvp_rays *rays, float *out_rgba,

@@ -48,7 +48,8 @@ class mvp_request(ctypes.Structure):
 class mvp_serve_info(ctypes.Structure):
     _fields_ = [("pending", c_int64), ("in_flight", c_int64), ("max_in_flight", c_int64), ("completed", c_int64),
                 ("resident_bytes", c_int64), ("in_flight_bytes", c_int64), ("grid_blocks", c_int32),
-                ("avatars", c_int32), ("device_status", c_int32), ("reserved", c_int32), ("batches", c_int64)]
+                ("avatars", c_int32), ("device_status", c_int32), ("reserved", c_int32), ("batches", c_int64),
+                ("cancelled", c_int64)]
 
 
 class MVPError(RuntimeError):
@@ -90,6 +91,7 @@ _SIGS = [
     ("mvp_serve_register_avatar", c_int32, [c_void_p, ctypes.POINTER(mvp_prims), ctypes.POINTER(c_int32)]),
     ("mvp_serve_submit", c_int32, [c_void_p, ctypes.POINTER(mvp_request), ctypes.POINTER(ctypes.c_uint64)]),
     ("mvp_serve_poll", c_int32, [c_void_p, ctypes.c_uint64, c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    ("mvp_serve_cancel", c_int32, [c_void_p, ctypes.c_uint64]),
     ("mvp_serve_wait", c_int32, [c_void_p, ctypes.c_uint64, ctypes.c_double, c_void_p,
                                  ctypes.POINTER(ctypes.c_double)]),
     ("mvp_serve_stats", c_int32, [c_void_p, ctypes.POINTER(mvp_serve_info)]),

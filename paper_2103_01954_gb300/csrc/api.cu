@@ -212,6 +212,8 @@ mvp_status mvp_ctx_sync(mvp_ctx *ctx, mvp_stream stream) {
       return fail(MVP_ERR_CAPACITY, "a kernel exceeded a capacity limit (a tile's BVH traversal stack of %d "
                                     "entries overflowed)",
                   mvp::STACK);
+    if (st & mvp::STATUS_POSE)
+      return fail(MVP_ERR_INVALID_ARG, "a primitive's pose defines no box (t, q or s not finite, q = 0 or s <= 0)");
     return fail(MVP_ERR_DEVICE, "device status word 0x%x", st);
   }
   return ok();
@@ -246,7 +248,8 @@ mvp_status mvp_build_bvh(mvp_ctx *ctx, const mvp_prims *prims, mvp_bvh *bvh, mvp
     e = mvp::bvh_reserve(bvh->b, prims->n);
     if (e != cudaSuccess) return cuda_fail(e, "BVH allocation");
   }
-  cudaError_t e = mvp::bvh_build(bvh->b, prims->t, prims->q, prims->s, prims->n, prims->M, (cudaStream_t)stream);
+  cudaError_t e = mvp::bvh_build(bvh->b, prims->t, prims->q, prims->s, prims->n, prims->M, (cudaStream_t)stream,
+                                 ctx->d_status);
   if (e != cudaSuccess) return cuda_fail(e, "BVH build launch");
   return ok();
 }

@@ -78,14 +78,38 @@ __device__ __forceinline__ uint32_t morton_code(const float *__restrict__ t, int
   return (spread10(qx) << 2) | (spread10(qy) << 1) | spread10(qz);
 }
 
-// Pose, march transform and world box of primitive k.
+// Pose, march transform and world box of primitive k. A pose that defines no box (a
+// non-finite value, a zero quaternion, a scale <= 0) sets STATUS_POSE and gets a
+// box no ray meets: an inverted world box (lo = +1e30 > hi = -1e30, neutral in the
+// nodes' unions and refused by the traversal) and a unit box centred at 1e30 for the
+// exact test, so the primitive is absent from every image and gradient.
 __device__ __forceinline__ void prim_setup(const float *__restrict__ t, const float *__restrict__ q,
                                            const float *__restrict__ s, int k, int M, Pose *__restrict__ pose,
-                                           Xform *__restrict__ xf, float4 *__restrict__ pbox) {
+                                           Xform *__restrict__ xf, float4 *__restrict__ pbox, int *status) {
   float tx = t[3 * k], ty = t[3 * k + 1], tz = t[3 * k + 2];
   float sx = s[3 * k], sy = s[3 * k + 1], sz = s[3 * k + 2];
+  const float qw = q[4 * k], qx = q[4 * k + 1], qy = q[4 * k + 2], qz = q[4 * k + 3];
+  const float qn = qw * qw + qx * qx + qy * qy + qz * qz;
+  const bool ok = isfinite(tx) && isfinite(ty) && isfinite(tz) && sx > 0.0f && sy > 0.0f && sz > 0.0f &&
+                  isfinite(sx) && isfinite(sy) && isfinite(sz) && qn > 0.0f && isfinite(qn);
+  if (!ok) {
+    if (status) atomicOr(status, STATUS_POSE);
+    const float far = 1.0e30f;
+    Pose P;
+    P.p0 = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+    P.p1 = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+    P.p2 = make_float4(1.0f, far, far, far);
+    P.p3 = make_float4(1.0f, 1.0f, 1.0f, 0.0f);
+    pose[k] = P;
+    Xform X;
+    X.r0 = X.r1 = X.r2 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    xf[k] = X;
+    pbox[2 * k] = make_float4(far, far, far, 0.0f);
+    pbox[2 * k + 1] = make_float4(-far, -far, -far, 0.0f);
+    return;
+  }
   float R[9];
-  rot_spec(q[4 * k], q[4 * k + 1], q[4 * k + 2], q[4 * k + 3], R);
+  rot_spec(qw, qx, qy, qz, R);
   Pose P;
   P.p0 = make_float4(R[0], R[1], R[2], R[3]);
   P.p1 = make_float4(R[4], R[5], R[6], R[7]);
@@ -133,11 +157,11 @@ __device__ __forceinline__ void prim_setup(const float *__restrict__ t, const fl
 __global__ void k_prims(const float *__restrict__ t, const float *__restrict__ q, const float *__restrict__ s,
                         int n, int M, const float *__restrict__ scene, Pose *__restrict__ pose,
                         Xform *__restrict__ xf, float4 *__restrict__ pbox, uint32_t *__restrict__ keys,
-                        int *__restrict__ vals) {
+                        int *__restrict__ vals, int *status) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const float sc[6] = {scene[0], scene[1], scene[2], scene[3], scene[4], scene[5]};
-  prim_setup(t, q, s, k, M, pose, xf, pbox);
+  prim_setup(t, q, s, k, M, pose, xf, pbox, status);
   keys[k] = morton_code(t, k, sc);
   vals[k] = k;
 }
@@ -147,12 +171,13 @@ __global__ void k_prims(const float *__restrict__ t, const float *__restrict__ q
 __global__ void __launch_bounds__(256) k_prims_partial(const float *__restrict__ t, const float *__restrict__ q,
                                                        const float *__restrict__ s, int n, int M,
                                                        Pose *__restrict__ pose, Xform *__restrict__ xf,
-                                                       float4 *__restrict__ pbox, float *__restrict__ partial) {
+                                                       float4 *__restrict__ pbox, float *__restrict__ partial,
+                                                       int *status) {
   __shared__ float sb[8][6];
   const int k = blockIdx.x * 256 + threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
   if (k < n) {
-    prim_setup(t, q, s, k, M, pose, xf, pbox);
+    prim_setup(t, q, s, k, M, pose, xf, pbox, status);
 #pragma unroll
     for (int j = 0; j < 3; ++j) b[j] = b[3 + j] = t[3 * k + j];
   }
@@ -690,7 +715,7 @@ void bvh_release(BvhBuffers &b) {
 }
 
 cudaError_t bvh_build(BvhBuffers &b, const float *t, const float *q, const float *s, int n, int M,
-                      cudaStream_t st) {
+                      cudaStream_t st, int *status) {
   b.n = n;
   b.M = M;
   if (n == 0) return cudaGetLastError();
@@ -705,12 +730,13 @@ cudaError_t bvh_build(BvhBuffers &b, const float *t, const float *q, const float
       attr_set = true;
     }
     float *partial = reinterpret_cast<float *>(b.counts);  // 6 floats per 256 primitives
-    k_prims_partial<<<n_partial, 256, 0, st>>>(t, q, s, n, M, b.pose, b.xf, b.pbox, partial);
+    k_prims_partial<<<n_partial, 256, 0, st>>>(t, q, s, n, M, b.pose, b.xf, b.pbox, partial, status);
     k_sort_one<<<1, SORT1_THREADS, SORT1_SMEM, st>>>(t, n, partial, n_partial, b.scene, b.keys_a, b.vals_a,
                                                      b.keys_b, b.vals_b);
   } else {
     k_bounds<<<1, 1024, 0, st>>>(t, n, b.scene);
-    k_prims<<<(n + 255) / 256, 256, 0, st>>>(t, q, s, n, M, b.scene, b.pose, b.xf, b.pbox, b.keys_a, b.vals_a);
+    k_prims<<<(n + 255) / 256, 256, 0, st>>>(t, q, s, n, M, b.scene, b.pose, b.xf, b.pbox, b.keys_a, b.vals_a,
+                                             status);
     uint32_t *kin = b.keys_a, *kout = b.keys_b;
     int *vin = b.vals_a, *vout = b.vals_b;
     for (int pass = 0; pass < 4; ++pass) {

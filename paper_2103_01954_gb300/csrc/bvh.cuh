@@ -29,7 +29,10 @@ struct BvhBuffers {
 
 cudaError_t bvh_reserve(BvhBuffers &b, int n);
 void bvh_release(BvhBuffers &b);
-cudaError_t bvh_build(BvhBuffers &b, const float *t, const float *q, const float *s, int n, int M, cudaStream_t st);
+// status (device, nullable): STATUS_POSE is or-ed in for a primitive whose pose
+// defines no box (non-finite, zero quaternion, scale <= 0).
+cudaError_t bvh_build(BvhBuffers &b, const float *t, const float *q, const float *s, int n, int M, cudaStream_t st,
+                      int *status);
 cudaError_t bvh_export(const BvhBuffers &b, uint64_t *keys, int32_t *children, float *bounds, float *scene,
                        cudaStream_t st);
 

@@ -21,6 +21,7 @@ constexpr unsigned FULL = 0xffffffffu;
 // Device status word bits.
 constexpr int STATUS_CAPACITY = 1;
 constexpr int STATUS_DEVICE = 2;
+constexpr int STATUS_POSE = 4;  // a primitive's t, q or s is not finite, |q| = 0 or s <= 0
 
 // Per-primitive pose as used by the membership test: R (row-major, R[3*i+j]),
 // t, 1/s (each correctly rounded). 64 bytes: p0 = {R00,R01,R02,R10},

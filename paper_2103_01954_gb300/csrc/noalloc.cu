@@ -115,7 +115,7 @@ extern "C" mvp_status mvp_raymarch_fwd_static(const mvp_prims *prims, const mvp_
   b.nodes = reinterpret_cast<mvp::Node *>(base + kOffNodes);
   b.parent = reinterpret_cast<int *>(base + kOffParent);
   b.rank = reinterpret_cast<int *>(base + kOffRank);
-  cudaError_t e = mvp::bvh_build(b, prims->t, prims->q, prims->s, prims->n, prims->M, st);
+  cudaError_t e = mvp::bvh_build(b, prims->t, prims->q, prims->s, prims->n, prims->M, st, d_status);
   if (e != cudaSuccess) return reject(MVP_ERR_CUDA, "BVH build launch failed");
 
   if (rays->n > 0) {

@@ -145,6 +145,7 @@ struct InFlight {
   size_t off = 0, bytes = 0;
   mvp_request req;
   clock_type::time_point submit;
+  bool detached = false;  // cancelled while running: freed by the server once done
 };
 
 // First-fit allocator over the image arena (host bookkeeping only).
@@ -213,7 +214,7 @@ struct mvp_server {
   std::deque<Pending> pending;
   std::map<uint64_t, InFlight> inflight;  // ticket -> request (admitted)
   size_t max_inflight_seen = 0;
-  uint64_t completed = 0, launches = 0;
+  uint64_t completed = 0, launches = 0, cancelled = 0;
 };
 
 namespace {
@@ -280,7 +281,24 @@ mvp_status launch(mvp_server *S, InFlight &f) {
 
 // Admit pending requests in FIFO order while a slot, budget and arena space allow,
 // launching each as it is admitted. Called with S->mu held.
+// Give an admitted request's slot, stream share and image memory back.
+void retire(mvp_server *S, std::map<uint64_t, InFlight>::iterator it) {
+  const InFlight &f = it->second;
+  S->arena.release(f.off, f.bytes);
+  S->inflight_bytes -= f.bytes;
+  S->outstanding[f.stream]--;
+  S->slot_busy[f.slot] = false;
+  S->inflight.erase(it);
+}
+
+bool is_done(mvp_server *S, const InFlight &f);
+
 mvp_status pump(mvp_server *S) {
+  for (auto it = S->inflight.begin(); it != S->inflight.end();) {  // cancelled requests that finished
+    auto nx = std::next(it);
+    if (it->second.detached && is_done(S, it->second)) retire(S, it);
+    it = nx;
+  }
   while (!S->pending.empty()) {
     Pending &p = S->pending.front();
     const size_t bytes = image_bytes(p.req);
@@ -404,11 +422,21 @@ mvp_status mvp_serve_register_avatar(mvp_server *S, const mvp_prims *prims, int3
   A.prims = *prims;
   cudaError_t e = mvp::bvh_reserve(A.bvh, prims->n);
   if (e != cudaSuccess) return serve_fail(MVP_ERR_OOM, "avatar BVH allocation");
-  e = mvp::bvh_build(A.bvh, prims->t, prims->q, prims->s, prims->n, prims->M, S->copy);
+  // the build's pose check goes to a word of its own (the first one collects the
+  // running requests' status bits)
+  int *pose_word = S->d_status + 1;
+  int bad = 0;
+  e = cudaMemsetAsync(pose_word, 0, sizeof(int), S->copy);
+  if (e == cudaSuccess) e = mvp::bvh_build(A.bvh, prims->t, prims->q, prims->s, prims->n, prims->M, S->copy, pose_word);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, pose_word, sizeof(int), cudaMemcpyDeviceToHost, S->copy);
   if (e == cudaSuccess) e = cudaStreamSynchronize(S->copy);
   if (e != cudaSuccess) {
     mvp::bvh_release(A.bvh);
     return serve_fail(MVP_ERR_CUDA, "avatar BVH build");
+  }
+  if (bad) {
+    mvp::bvh_release(A.bvh);
+    return serve_fail(MVP_ERR_INVALID_ARG, "avatar pose defines no box (t, q or s not finite, q = 0 or s <= 0)");
   }
   const size_t vb = prims->dtype == MVP_F32 ? 16 : 8;
   A.bytes = (size_t)prims->n * prims->M * prims->M * prims->M * vb + A.bvh.bytes;
@@ -457,6 +485,7 @@ mvp_status mvp_serve_poll(mvp_server *S, uint64_t ticket, float *out_rgba, doubl
   std::lock_guard<std::mutex> lk(S->mu);
   cudaSetDevice(S->device);
   auto it = S->inflight.find(ticket);
+  if (it != S->inflight.end() && it->second.detached) return serve_fail(MVP_ERR_INVALID_ARG, "cancelled ticket");
   if (it == S->inflight.end()) {
     for (auto &p : S->pending)
       if (p.ticket == ticket) {
@@ -477,12 +506,30 @@ mvp_status mvp_serve_poll(mvp_server *S, uint64_t ticket, float *out_rgba, doubl
     if (e != cudaSuccess) return serve_fail(MVP_ERR_CUDA, "image copy");
   }
   if (latency_ms) *latency_ms = ms;
-  S->arena.release(f.off, f.bytes);
-  S->inflight_bytes -= f.bytes;
-  S->outstanding[f.stream]--;
-  S->slot_busy[f.slot] = false;
-  S->inflight.erase(it);
+  retire(S, it);
   S->completed++;
+  mvp_status st = pump(S);
+  return st ? st : MVP_OK;
+}
+
+mvp_status mvp_serve_cancel(mvp_server *S, uint64_t ticket) {
+  if (!S) return serve_fail(MVP_ERR_INVALID_ARG, "NULL server");
+  std::lock_guard<std::mutex> lk(S->mu);
+  cudaSetDevice(S->device);
+  for (auto p = S->pending.begin(); p != S->pending.end(); ++p)
+    if (p->ticket == ticket) {  // never admitted: nothing ran
+      S->pending.erase(p);
+      S->cancelled++;
+      return MVP_OK;
+    }
+  auto it = S->inflight.find(ticket);
+  if (it == S->inflight.end() || it->second.detached) return serve_fail(MVP_ERR_INVALID_ARG, "unknown ticket");
+  S->cancelled++;
+  if (is_done(S, it->second)) {
+    retire(S, it);
+  } else {
+    it->second.detached = true;  // its launch runs to completion; the memory is freed after
+  }
   mvp_status st = pump(S);
   return st ? st : MVP_OK;
 }
@@ -505,6 +552,7 @@ mvp_status mvp_serve_stats(mvp_server *S, mvp_serve_info *info) {
   info->in_flight = (int64_t)S->inflight.size();
   info->max_in_flight = (int64_t)S->max_inflight_seen;
   info->completed = (int64_t)S->completed;
+  info->cancelled = (int64_t)S->cancelled;
   info->resident_bytes = (int64_t)S->resident;
   info->in_flight_bytes = (int64_t)S->inflight_bytes;
   info->grid_blocks = S->grid;

@@ -227,7 +227,8 @@ __device__ __forceinline__ bool traverse_tile(SH &sh, const Node *__restrict__ n
         l = __float_as_int(a.w);
         r = __float_as_int(b.w);
         leaf = l < 0;
-        pass = packet_hits_box(P, a, b, ta, tb);
+        // an inverted box holds no primitive that any ray can meet
+        pass = a.x <= b.x && packet_hits_box(P, a, b, ta, tb);
       }
       unsigned mleaf = __ballot_sync(FULL, pass && leaf);
       unsigned minner = __ballot_sync(FULL, pass && !leaf);

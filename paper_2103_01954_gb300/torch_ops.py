@@ -342,6 +342,10 @@ class Server:
         st = B.lib().mvp_serve_wait(self.handle, ticket, float(timeout_ms), _ptr(out), ctypes.byref(lat))
         return st, lat.value
 
+    def cancel(self, ticket: int) -> None:
+        """Withdraw a request (queued: dropped; running: finishes, then freed)."""
+        B.check(B.lib().mvp_serve_cancel(self.handle, ctypes.c_uint64(ticket)), "mvp_serve_cancel")
+
     def stats(self) -> dict:
         info = B.mvp_serve_info()
         B.check(B.lib().mvp_serve_stats(self.handle, ctypes.byref(info)), "mvp_serve_stats")

@@ -344,3 +344,35 @@ def test_paper_scale_sampled_pixels(cfg):
     ref = oracle.render(sc, sub, F32M)["rgba"]
     _check_image(o[sel], ref, cfg)
     assert (ref[:, 3] > 0).mean() > 0.3
+
+
+def test_degenerate_poses_reported():
+    """A NaN centre, a zero quaternion and a negative scale are reported by the next
+    sync (MVP_ERR_INVALID_ARG) and refused by avatar registration; those primitives are
+    absent: the frame equals the oracle's image of the scene without them."""
+    sc, rays, _ = synthetic.make_config("small_512x8^3_96x128", 4)
+    bad = sc.t.copy(), sc.q.copy(), sc.s.copy()
+    bad[0][5, 1] = np.nan
+    bad[1][17] = 0.0
+    bad[2][40, 2] = -sc.s[40, 2]
+    sc_bad = synthetic.Scene(t=bad[0], q=bad[1], s=bad[2], payload=sc.payload, M=sc.M)
+    dv = Dev(sc_bad, rays)
+    dv.bvh.build(dv.prims)
+    with pytest.raises(B.MVPError) as ei:
+        dv.ctx.sync()
+    assert ei.value.status == B.MVP_ERR_INVALID_ARG
+    out, _ = T.raymarch_fwd(dv.ctx, dv.prims, dv.bvh, dv.rs)
+    dv.ctx.sync()  # the status word was cleared; the render itself reports nothing
+    keep = np.setdiff1d(np.arange(sc.n), [5, 17, 40])
+    ok = synthetic.Scene(t=sc.t[keep], q=sc.q[keep], s=sc.s[keep], payload=sc.payload[keep], M=sc.M)
+    ref = oracle.render(ok, rays, F32M)["rgba"]
+    _check_image(out.cpu().numpy(), ref, "degenerate poses")
+    # the bad primitives were in view: the image without them differs from the full one
+    full = oracle.render(sc, rays, F32M)["rgba"]
+    assert np.abs(full - ref).max() > 1e-2
+    srv = T.Server(dv.ctx, hbm_budget=1 << 30, max_slots=2)
+    with pytest.raises(B.MVPError) as ei:
+        srv.register(dv.t, dv.q, dv.s, dv.payload)
+    assert ei.value.status == B.MVP_ERR_INVALID_ARG
+    assert srv.register(*(torch.from_numpy(x).cuda() for x in (sc.t, sc.q, sc.s, sc.payload))) == 0
+    srv.close()

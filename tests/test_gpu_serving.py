@@ -219,3 +219,36 @@ def test_request_payload_override():
     assert ei.value.status == B.MVP_ERR_INVALID_ARG
     assert srv.stats()["device_status"] == 0
     srv.close()
+
+
+def test_cancel_queued_and_running_requests():
+    """A queued request is dropped before it runs; a running one finishes and is freed
+    by the server; both tickets become unknown; the others complete unchanged."""
+    torch.cuda.set_device(0)
+    ctx = T.Context(0)
+    av = _avatars(ctx)[0]
+    srv = T.Server(ctx, hbm_budget=2 << 30, max_slots=2)
+    aid = srv.register(*av)
+    w, h = 200, 160
+    cams = _cams(6, 21)
+    tks = [srv.submit_raw(T.Server.request(aid, c, float(w), w, h, T_NEAR, T_FAR, DT)) for c in cams]
+    st = srv.stats()
+    assert st["in_flight"] + st["pending"] == 6 and st["pending"] >= 4  # two slots
+    srv.cancel(tks[4])  # queued
+    srv.cancel(tks[0])  # admitted (running or done)
+    for tk in (tks[0], tks[4]):
+        with pytest.raises(B.MVPError) as ei:
+            srv.poll(tk)
+        assert ei.value.status == B.MVP_ERR_INVALID_ARG
+        with pytest.raises(B.MVPError):
+            srv.cancel(tk)
+    for i in (1, 2, 3, 5):
+        img = torch.empty((h * w, 4), dtype=torch.float32, device=DEV)
+        st, _ = srv.wait(tks[i], 10000.0, img)
+        assert st == B.MVP_OK
+        assert (img - _reference(ctx, av, cams[i], float(w), w, h)).abs().max().item() <= 1e-5
+    st = srv.stats()
+    assert st["cancelled"] == 2 and st["completed"] == 4
+    assert st["pending"] == 0 and st["in_flight"] == 0 and st["in_flight_bytes"] == 0
+    assert st["device_status"] == 0
+    srv.close()
