@@ -103,7 +103,7 @@ typedef struct mvp_rays {
   float bg[3];          /* constant background colour */
   int32_t width;        /* if width * height == n: rays form a row-major image  */
   int32_t height;       /* and are marched in 2-D pixel tiles; else 1-D groups  */
-  int32_t flags;        /* 0, or MVP_BLEND_SEQUENTIAL */
+  int32_t flags;        /* 0, or MVP_BLEND_SEQUENTIAL | MVP_COMPOSITE_LITERAL */
 } mvp_rays;
 
 /* mvp_rays.flags: blend the primitives that share a ray's saturating sample one by
@@ -112,6 +112,11 @@ typedef struct mvp_rays {
  * clamping once. Every other sample is unaffected (the two rules agree wherever T
  * stays below 1). Forward only: mvp_raymarch_bwd rejects it. */
 #define MVP_BLEND_SEQUENTIAL 1
+/* mvp_rays.flags: the background composite read literally as I~ = A I + (1 - A) B
+ * (Sec. 3.1.4) instead of I~ = I + (1 - A) B, which treats the marched I as already
+ * weighted by the accumulated opacity (its integrand carries dT). Forward only:
+ * mvp_raymarch_bwd rejects it. */
+#define MVP_COMPOSITE_LITERAL 2
 
 typedef struct mvp_ctx mvp_ctx;
 typedef struct mvp_bvh mvp_bvh;

@@ -18,4 +18,5 @@ from .oracle import (  # noqa: F401
     MEMBER_F64,
     MEMBER_F32,
     SEQUENTIAL,
+    LITERAL,
 )

@@ -46,7 +46,8 @@
  *   R3 s_k are half extents: x = t_k + R_k diag(s_k) y with y in [-1,1]^3.
  *   R4 corner-aligned voxels: u = (y+1)/2*(M-1), cell i0 = min(floor(u), M-2).
  *   R5 I_p is already weighted by dT, so the background composite is
- *      I~ = I + (1 - A) B.
+ *      I~ = I + (1 - A) B. Mode bit3 (ORC_LITERAL) reads the printed composite
+ *      literally instead: I~ = A I + (1 - A) B.
  */
 #include <math.h>
 #include <stdint.h>
@@ -300,6 +301,7 @@ typedef struct {
 } scene_t;
 
 #define ORC_SEQUENTIAL 4
+#define ORC_LITERAL 8 /* composite A I + (1 - A) B instead of I + (1 - A) B */
 
 /* One primitive's trilinear RGBA at the current sample (sequential blending). */
 typedef struct {
@@ -621,7 +623,8 @@ int orc_render(int n, int M, const float *t, const float *q, const float *s, con
       ray_out_t res;
       march_ray(&sc, &m, r, mode, cands, seq, &res);
       double A = res.T;
-      for (int c = 0; c < 3; ++c) out[4 * r + c] = res.rgb[c] + (1.0 - A) * (double)bg[c];
+      for (int c = 0; c < 3; ++c)
+        out[4 * r + c] = ((mode & ORC_LITERAL) ? A * res.rgb[c] : res.rgb[c]) + (1.0 - A) * (double)bg[c];
       out[4 * r + 3] = A;
       if (near_face) near_face[r] = (uint8_t)res.near_face;
       if (n_eval) n_eval[r] = res.n_eval;
@@ -677,7 +680,7 @@ int orc_backward(int n, int M, const float *t, const float *q, const float *s, c
                  float eps, const float *bg, int n_steps, int mode, int n_threads,
                  const double *grad_out, double *g_payload, double *g_t, double *g_q, double *g_s) {
   if (n < 0 || M < 2 || n_rays < 0 || !(dt > 0) || n_steps < 0) return -1;
-  if (mode & ORC_SEQUENTIAL) return -1; /* the adjoint follows the summed rule only */
+  if (mode & (ORC_SEQUENTIAL | ORC_LITERAL)) return -1; /* summed rule, premultiplied composite only */
   scene_t sc;
   if (scene_init(&sc, n, M, t, q, s, payload)) return -1;
   march_t m = {o, d, t_near, t_far, dt, eps, {bg[0], bg[1], bg[2]}, n_steps};

@@ -20,6 +20,7 @@ MODE_PRUNED = 1
 MEMBER_F64 = 0
 MEMBER_F32 = 2
 SEQUENTIAL = 4  # the saturating sample blended primitive by primitive in BVH order
+LITERAL = 8  # background composite A I + (1 - A) B
 
 _lib = None
 

@@ -25,6 +25,7 @@ MVP_ERR_DEVICE = -6
 
 MVP_F32, MVP_BF16, MVP_F16 = 0, 1, 2
 MVP_BLEND_SEQUENTIAL = 1
+MVP_COMPOSITE_LITERAL = 2
 
 
 class mvp_prims(ctypes.Structure):

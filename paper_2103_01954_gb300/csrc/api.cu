@@ -73,7 +73,8 @@ mvp_status check_rays(const mvp_rays *r, int64_t *n_steps) {
   if (!(r->t_far > r->t_near)) return fail(MVP_ERR_INVALID_ARG, "rays.t_far must be > t_near");
   if (!(r->eps_early >= 0.0f && r->eps_early < 1.0f)) return fail(MVP_ERR_INVALID_ARG, "rays.eps_early not in [0, 1)");
   if (r->width < 0 || r->height < 0) return fail(MVP_ERR_INVALID_ARG, "rays.width/height < 0");
-  if (r->flags & ~MVP_BLEND_SEQUENTIAL) return fail(MVP_ERR_INVALID_ARG, "rays.flags has unknown bits");
+  if (r->flags & ~(MVP_BLEND_SEQUENTIAL | MVP_COMPOSITE_LITERAL))
+    return fail(MVP_ERR_INVALID_ARG, "rays.flags has unknown bits");
   for (int c = 0; c < 3; ++c)
     if (!finite(r->bg[c])) return fail(MVP_ERR_INVALID_ARG, "rays.bg must be finite");
   int64_t ns = mvp_num_steps(r->t_near, r->t_far, r->dt);
@@ -102,6 +103,7 @@ mvp::MarchArgs march_args(mvp_ctx *ctx, const mvp_prims *p, const mvp_bvh *bvh, 
   a.xf = bvh->b.xf;
   a.rank = bvh->b.rank;
   a.sequential = (r->flags & MVP_BLEND_SEQUENTIAL) ? 1 : 0;
+  a.literal = (r->flags & MVP_COMPOSITE_LITERAL) ? 1 : 0;
   a.geom = mvp::make_tile_geom(r->n, r->width, r->height);
   a.o = r->o;
   a.d = r->d;
@@ -312,6 +314,8 @@ mvp_status mvp_raymarch_bwd(mvp_ctx *ctx, const mvp_prims *prims, mvp_bvh *bvh, 
   if (rays->n > 0 && (!saved || !grad_rgba)) return fail(MVP_ERR_INVALID_ARG, "saved and grad_rgba are required");
   if (rays->flags & MVP_BLEND_SEQUENTIAL)
     return fail(MVP_ERR_INVALID_ARG, "the adjoint supports the summed blending rule only");
+  if (rays->flags & MVP_COMPOSITE_LITERAL)
+    return fail(MVP_ERR_INVALID_ARG, "the adjoint supports the premultiplied composite only");
   if (reinterpret_cast<uintptr_t>(g_payload) % 16 || reinterpret_cast<uintptr_t>(grad_rgba) % 16 ||
       reinterpret_cast<uintptr_t>(saved) % 8)
     return fail(MVP_ERR_INVALID_ARG, "g_payload and grad_rgba must be 16-byte aligned, saved 8-byte aligned");

@@ -23,6 +23,7 @@ struct MarchArgs {
   const Xform *xf;
   const int *rank;  // leaf position of each primitive (BVH order)
   int sequential;   // blend a ray's saturating sample in BVH order (MVP_BLEND_SEQUENTIAL)
+  int literal;      // composite A I + (1 - A) B (MVP_COMPOSITE_LITERAL) instead of I + (1 - A) B
   // rays
   TileGeom geom;
   const float *o, *d;

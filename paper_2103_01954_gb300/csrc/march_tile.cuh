@@ -349,6 +349,11 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
     return;
   }
   const float bgw = 1.0f - T;
+  if (a.literal) {  // the composite read with I not yet weighted by A
+    Ir *= T;
+    Ig *= T;
+    Ib *= T;
+  }
   float4 out = make_float4(fmaf(bgw, a.bg[0], Ir), fmaf(bgw, a.bg[1], Ig), fmaf(bgw, a.bg[2], Ib), T);
   reinterpret_cast<float4 *>(a.out)[L.r] = out;
   if (a.saved && !saved_done) {

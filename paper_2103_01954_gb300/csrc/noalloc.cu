@@ -76,7 +76,7 @@ extern "C" mvp_status mvp_raymarch_fwd_static(const mvp_prims *prims, const mvp_
   if (reinterpret_cast<uintptr_t>(out_rgba) % 16) return reject(MVP_ERR_INVALID_ARG, "out_rgba is misaligned");
   if (!(rays->dt > 0.0f) || !(rays->t_far > rays->t_near) || !(rays->eps_early >= 0.0f && rays->eps_early < 1.0f) ||
       !isfinite(rays->t_near) || !isfinite(rays->t_far) || !isfinite(rays->dt) || rays->width < 0 || rays->height < 0 ||
-      (rays->flags & ~MVP_BLEND_SEQUENTIAL))
+      (rays->flags & ~(MVP_BLEND_SEQUENTIAL | MVP_COMPOSITE_LITERAL)))
     return reject(MVP_ERR_INVALID_ARG, "bad ray parameters");
   const int64_t ns = mvp_num_steps(rays->t_near, rays->t_far, rays->dt);
   if (ns > MVP_MAX_STEPS) return reject(MVP_ERR_INVALID_ARG, "n_steps exceeds MVP_MAX_STEPS");
@@ -130,6 +130,7 @@ extern "C" mvp_status mvp_raymarch_fwd_static(const mvp_prims *prims, const mvp_
     a.xf = b.xf;
     a.rank = b.rank;
     a.sequential = (rays->flags & MVP_BLEND_SEQUENTIAL) ? 1 : 0;
+    a.literal = (rays->flags & MVP_COMPOSITE_LITERAL) ? 1 : 0;
     a.geom = mvp::make_tile_geom(rays->n, rays->width, rays->height);
     a.o = rays->o;
     a.d = rays->d;

@@ -48,12 +48,15 @@ def prims_struct(t, q, s, payload) -> B.mvp_prims:
 
 
 def rays_struct(o, d, t_near, t_far, dt, eps_early=0.0, bg=(0.0, 0.0, 0.0), width=0, height=0,
-                sequential=False) -> B.mvp_rays:
-    """mvp_rays; sequential=True blends a ray's saturating sample in BVH order."""
+                sequential=False, literal_composite=False) -> B.mvp_rays:
+    """mvp_rays; sequential=True blends a ray's saturating sample in BVH order;
+    literal_composite=True composites A I + (1 - A) B."""
     _need(o, "o", torch.float32, (3,))
     _need(d, "d", torch.float32, (3,))
     r = B.mvp_rays(n=o.shape[0], o=_ptr(o), d=_ptr(d), t_near=t_near, t_far=t_far, dt=dt, eps_early=eps_early,
-                   width=width, height=height, flags=B.MVP_BLEND_SEQUENTIAL if sequential else 0)
+                   width=width, height=height,
+                   flags=(B.MVP_BLEND_SEQUENTIAL if sequential else 0) |
+                   (B.MVP_COMPOSITE_LITERAL if literal_composite else 0))
     r.bg[0], r.bg[1], r.bg[2] = bg
     return r
 

@@ -186,6 +186,24 @@ def test_forward_eps_and_background(eps, bg):
         assert (err <= 2e-4).mean() >= 0.99
 
 
+def test_forward_literal_composite():
+    """MVP_COMPOSITE_LITERAL: A I + (1 - A) B, against the oracle's literal mode."""
+    sc, rays, _ = synthetic.make_config("small_512x8^3_96x128", 2)
+    rays.bg = (0.25, 0.5, 1.0)
+    dv = Dev(sc, rays)
+    dv.rs = T.rays_struct(dv.o, dv.d, literal_composite=True, **dv.params)
+    out, _ = dv.build().render()
+    ref = oracle.render(sc, rays, F32M | oracle.LITERAL)["rgba"]
+    _check_image(out.cpu().numpy(), ref, "literal composite")
+    pre = oracle.render(sc, rays, F32M)["rgba"]
+    assert np.abs(ref - pre).max() > 1e-2
+    g = torch.zeros_like(out)
+    _, saved = T.raymarch_fwd(dv.ctx, dv.prims, dv.bvh, dv.rs, want_saved=True)
+    with pytest.raises(B.MVPError) as ei:
+        T.raymarch_bwd(dv.ctx, dv.prims, dv.bvh, dv.rs, saved, g)
+    assert ei.value.status == B.MVP_ERR_INVALID_ARG
+
+
 def test_forward_empty_scene_and_zero_payload():
     sc, rays, _ = synthetic.make_config("tiny_8x8^3_64x64", 0)
     rays.bg = (0.1, 0.2, 0.3)

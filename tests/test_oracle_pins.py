@@ -328,6 +328,32 @@ def test_order_free_sum_within_sample(orc):
     np.testing.assert_allclose(a, b, atol=1e-12)
 
 
+def test_literal_composite(orc):
+    """Mode bit 3 reads the composite as A I + (1 - A) B (Sec. 3.1.4 printed literally):
+    on the uniform box I = c A, so the literal reading gives c A^2 + (1 - A) B; on a
+    scene, only the background composite changes."""
+    g = json.load(open(os.path.join(GOLDEN, "uniform_box.json")))
+    b, r = g["box"], g["ray"]
+    bg = (0.25, 0.5, 1.0)
+    for case in g["cases"]:
+        sc = single_box(M=b["M"], alpha=case["sigma"], rgb=b["rgb"], t=b["t"], q=b["q"], s=b["s"])
+        rays = rays_from(r["o"], r["d"], r["t_near"], r["t_far"], r["dt"], eps=case["eps"], bg=bg)
+        out = orc.render(sc, rays, PRUNED64 | 8)["rgba"][0]
+        A = case["A"]
+        expect = np.float32(b["rgb"]).astype(np.float64) * A * A + (1 - A) * np.float32(bg).astype(np.float64)
+        assert abs(out[3] - A) < g["tolerance"]
+        np.testing.assert_allclose(out[:3], expect, atol=2 * g["tolerance"])
+    sc, rays, _ = synthetic.make_config("tiny_8x8^3_64x64", 3)
+    rays.bg = bg
+    pre = orc.render(sc, rays, PRUNED32)["rgba"]
+    lit = orc.render(sc, rays, PRUNED32 | 8)["rgba"]
+    B = np.float32(bg).astype(np.float64)[None]
+    A = pre[:, 3:4]
+    np.testing.assert_array_equal(lit[:, 3], pre[:, 3])
+    np.testing.assert_allclose(lit[:, :3], A * (pre[:, :3] - (1 - A) * B) + (1 - A) * B, atol=1e-12)
+    assert np.abs(lit - pre).max() > 1e-3
+
+
 # --------------------------------------------------------------------------- modes agree
 @pytest.mark.parametrize("member", [0, 2])
 def test_brute_equals_pruned(orc, member):
