@@ -142,6 +142,12 @@ MVP_API void mvp_ctx_destroy(mvp_ctx *ctx);
  * stream reported an error). */
 #define MVP_STATUS_CAPACITY 1
 #define MVP_STATUS_POSE 4
+/* Checked builds only (compiled with -DMVP_CHECK_BOUNDS, the library's stand-in for a
+ * memory checker): an index fell outside its array; the access was skipped.
+ * mvp_ctx_sync reports it as MVP_ERR_DEVICE. */
+#define MVP_STATUS_BOUNDS 8
+/* 1 if this library is a checked build, else 0. */
+MVP_API int32_t mvp_bounds_checked(void);
 MVP_API mvp_status mvp_ctx_sync(mvp_ctx *ctx, mvp_stream stream);
 
 /* ------------------------------------------------------ BVH (Sec. 3.2.1) */

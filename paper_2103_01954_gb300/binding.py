@@ -102,6 +102,7 @@ _SIGS = [
                                    c_void_p]),
     ("mvp_assemble_payload", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_float,
                                        c_int32, c_void_p]),
+    ("mvp_bounds_checked", c_int32, []),
     ("mvp_axis_angle_to_quat", c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     ("mvp_axis_angle_backward", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     ("mvp_volume_prior", c_int32, [c_void_p, c_void_p, c_int32, c_float, c_void_p, c_void_p, c_void_p]),
@@ -109,7 +110,9 @@ _SIGS = [
 
 
 def library_path() -> str:
-    return _build.build()
+    """The library to load: the checked build (device-side bounds checks) when the
+    environment sets MVP_CHECK_BOUNDS=1, else the release build."""
+    return _build.build(checked=os.environ.get("MVP_CHECK_BOUNDS") == "1")
 
 
 def lib():

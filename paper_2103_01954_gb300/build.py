@@ -59,18 +59,19 @@ def sources_digest(names: list[str]) -> str:
     return h.hexdigest()[:16]
 
 
-def library_path() -> str:
-    return os.path.join(BUILD, f"libmvp_{_digest()}.so")
+def library_path(checked: bool = False) -> str:
+    return os.path.join(BUILD, f"libmvp_{_digest()}{'_checked' if checked else ''}.so")
 
 
-def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Build (if needed) and return the path of libmvp.so."""
-    out = library_path()
+def build(verbose: bool = False, extra_flags: list[str] | None = None, checked: bool = False) -> str:
+    """Build (if needed) and return the path of libmvp.so. checked: the variant with
+    device-side bounds checks (-DMVP_CHECK_BOUNDS), a library of its own."""
+    out = library_path(checked)
     if os.path.exists(out) and not extra_flags:
         return out
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    flags = ARCH + NVCC_FLAGS + (extra_flags or [])
+    flags = ARCH + NVCC_FLAGS + (["-DMVP_CHECK_BOUNDS"] if checked else []) + (extra_flags or [])
     objs = []
     jobs = []
     for src in _sources():
@@ -93,7 +94,7 @@ def build(verbose: bool = False, extra_flags: list[str] | None = None) -> str:
         os.remove(o)
     # libraries of earlier sources are stale (a process that loaded one keeps its mapping)
     for old in glob.glob(os.path.join(BUILD, "libmvp_*.so")):
-        if old != out:
+        if old not in (library_path(False), library_path(True)):
             try:
                 os.remove(old)
             except OSError:

@@ -200,6 +200,14 @@ void mvp_ctx_destroy(mvp_ctx *ctx) {
   delete ctx;
 }
 
+int32_t mvp_bounds_checked(void) {
+#ifdef MVP_CHECK_BOUNDS
+  return 1;
+#else
+  return 0;
+#endif
+}
+
 mvp_status mvp_ctx_sync(mvp_ctx *ctx, mvp_stream stream) {
   if (!ctx) return fail(MVP_ERR_INVALID_ARG, "ctx is NULL");
   DeviceGuard g(ctx->device);
@@ -214,6 +222,8 @@ mvp_status mvp_ctx_sync(mvp_ctx *ctx, mvp_stream stream) {
       return fail(MVP_ERR_CAPACITY, "a kernel exceeded a capacity limit (a tile's BVH traversal stack of %d "
                                     "entries overflowed)",
                   mvp::STACK);
+    if (st & mvp::STATUS_BOUNDS)
+      return fail(MVP_ERR_DEVICE, "an index fell outside its array (checked build; the access was skipped)");
     if (st & mvp::STATUS_POSE)
       return fail(MVP_ERR_INVALID_ARG, "a primitive's pose defines no box (t, q or s not finite, q = 0 or s <= 0)");
     return fail(MVP_ERR_DEVICE, "device status word 0x%x", st);

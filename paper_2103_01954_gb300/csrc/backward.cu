@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
     int w1 = min(a.n_steps, w0 + wlen);
     int ne = build_window<CAP>(sh, a.nodes, a.pose, a.xf, reinterpret_cast<const char *>(a.payload), prim_bytes,
                                a.n_prims, L, valid ? i_last : -1, a.t_near, a.t_far, a.dt, a.n_steps, w0, w1,
-                               skip);
+                               skip, a.status);
     if (ne == WINDOW_STACK) {
       if (lane == 0) atomicOr(a.status, STATUS_CAPACITY);
       return;
@@ -121,6 +121,7 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
           fy = uy - (float)iy;
           fz = uz - (float)iz;
           vo = iz * M2 + iy * M + ix;  // voxel within the primitive
+          if (!MVP_IN_BOUNDS(vo >= 0 && vo + M2 + M + 1 < M2 * M, a.status)) continue;
           if (vo != held) {            // consecutive samples often stay in one cell
             c000 = Voxel<DT>::load(pbase, vo);
             c001 = Voxel<DT>::load(pbase, vo + 1);

@@ -22,6 +22,20 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int STATUS_CAPACITY = 1;
 constexpr int STATUS_DEVICE = 2;
 constexpr int STATUS_POSE = 4;  // a primitive's t, q or s is not finite, |q| = 0 or s <= 0
+constexpr int STATUS_BOUNDS = 8;  // checked builds: an index fell outside its array (access skipped)
+
+// Checked builds (-DMVP_CHECK_BOUNDS, the stand-in for a memory checker): an index
+// outside its array sets STATUS_BOUNDS and the access is skipped. Elsewhere the
+// check compiles to nothing.
+#ifdef MVP_CHECK_BOUNDS
+__device__ __forceinline__ bool in_bounds(bool ok, int *status) {
+  if (!ok && status) atomicOr(status, STATUS_BOUNDS);
+  return ok;
+}
+#define MVP_IN_BOUNDS(cond, status) ::mvp::in_bounds((cond), (status))
+#else
+#define MVP_IN_BOUNDS(cond, status) true
+#endif
 
 // Per-primitive pose as used by the membership test: R (row-major, R[3*i+j]),
 // t, 1/s (each correctly rounded). 64 bytes: p0 = {R00,R01,R02,R10},

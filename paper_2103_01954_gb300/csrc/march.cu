@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(TILE_WARPS * 32) k_hits(HitArgs a) {
       return true;
     };
     float slack = 1.0e-5f * (fabsf(ta) + fabsf(tb)) + 1.0e-30f;
-    bool ok = traverse_tile(sh, a.nodes, a.n_prims, ta - slack, tb + slack, emit);
+    bool ok = traverse_tile(sh, a.nodes, a.n_prims, ta - slack, tb + slack, emit, a.status);
     __syncwarp();
     if (!ok) {
       count = c0;  // drop this window's partial output and retry a narrower one

@@ -31,7 +31,7 @@ struct VoxelBytes {
 // point x: the arithmetic of the chunked loop in march_tile, rounding for rounding.
 template <int DT, int MT>
 __device__ __forceinline__ float4 sample_rgba(const Xform &X, const char *pbase, const float x[3], int Mr,
-                                              float Mm1) {
+                                              float Mm1, int *status = nullptr) {
   const int M = MT > 0 ? MT : Mr;
   float ux = fmaf(X.r0.x, x[0], fmaf(X.r0.y, x[1], fmaf(X.r0.z, x[2], X.r0.w)));
   float uy = fmaf(X.r1.x, x[0], fmaf(X.r1.y, x[1], fmaf(X.r1.z, x[2], X.r1.w)));
@@ -41,6 +41,7 @@ __device__ __forceinline__ float4 sample_rgba(const Xform &X, const char *pbase,
   uz = fminf(fmaxf(uz, 0.0f), Mm1);
   const int ix = min((int)ux, M - 2), iy = min((int)uy, M - 2), iz = min((int)uz, M - 2);
   const int v = (iz * M + iy) * M + ix;
+  if (!MVP_IN_BOUNDS(v >= 0 && v + M * M + M + 1 < M * M * M, status)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const void *p = pbase;
   const float4 c000 = Voxel<DT>::load(p, v), c001 = Voxel<DT>::load(p, v + 1);
   const float4 c010 = Voxel<DT>::load(p, v + M), c011 = Voxel<DT>::load(p, v + M + 1);
@@ -90,7 +91,7 @@ __device__ __forceinline__ bool sample_all(SH &sh, const MarchArgs &a, const Lan
       X.r0 = __ldg(xp);
       X.r1 = __ldg(xp + 1);
       X.r2 = __ldg(xp + 2);
-      const float4 val = sample_rgba<DT, MT>(X, payload + (int64_t)k * prim_bytes, xs, M, Mm1);
+      const float4 val = sample_rgba<DT, MT>(X, payload + (int64_t)k * prim_bytes, xs, M, Mm1, a.status);
       rg = __ffma2_rn(splat2(val.w), lo2(val), rg);
       ba = __ffma2_rn(make_float2(val.w, 1.0f), hi2(val), ba);
       ++nec;
@@ -98,7 +99,7 @@ __device__ __forceinline__ bool sample_all(SH &sh, const MarchArgs &a, const Lan
     return true;
   };
   const float slack = 2.0e-5f * fabsf(ti) + 1.0e-30f;
-  const bool ok = traverse_tile(sh, a.nodes, a.n_prims, ti - slack, ti + slack, emit);
+  const bool ok = traverse_tile(sh, a.nodes, a.n_prims, ti - slack, ti + slack, emit, a.status);
   __syncwarp();
   return ok;
 }
@@ -136,7 +137,7 @@ __device__ __forceinline__ void blend_sequential(const TileShared<CAP> &sh, int 
     const int e = sh.cand[p];
     const uint32_t r = sh.erng[e][lane];
     if ((int)(r & 0xffffu) > ii || (int)(r >> 16) < ii) continue;
-    const float4 v = sample_rgba<DT, MT>(sh.exf[e], sh.eptr[e], x, M, Mm1);
+    const float4 v = sample_rgba<DT, MT>(sh.exf[e], sh.eptr[e], x, M, Mm1, a.status);
     const float w = fminf(v.w * a.dt, rem);
     Ir = fmaf(v.x, w, Ir);
     Ig = fmaf(v.y, w, Ig);
@@ -206,7 +207,7 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
     int w1 = min(a.n_steps, w0 + wlen);
     int lane_last = alive ? a.n_steps - 1 : -1;
     int ne = build_window<CAP>(sh, a.nodes, a.pose, a.xf, reinterpret_cast<const char *>(a.payload), prim_bytes,
-                               a.n_prims, L, lane_last, a.t_near, a.t_far, a.dt, a.n_steps, w0, w1);
+                               a.n_prims, L, lane_last, a.t_near, a.t_far, a.dt, a.n_steps, w0, w1, 0, a.status);
     if (ne == WINDOW_STACK) {
       stack_full = true;
       break;
@@ -290,6 +291,7 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
           uz = fminf(fmaxf(uz, 0.0f), Mm1);
           const int ix = min((int)ux, M - 2), iy = min((int)uy, M - 2), iz = min((int)uz, M - 2);
           const int v = (iz * M + iy) * M + ix;
+          if (!MVP_IN_BOUNDS(v >= 0 && v + M * M + M + 1 < M * M * M, a.status)) continue;
           if (v != held) {
             const void *p = pbase;
             c000 = Voxel<DT>::load(p, v);

@@ -205,7 +205,7 @@ struct TileShared {
 // to abort. Returns false on stack overflow or an aborted emit.
 template <class SH, class Emit>
 __device__ __forceinline__ bool traverse_tile(SH &sh, const Node *__restrict__ nodes, int n_prims, float ta,
-                                              float tb, Emit &&emit) {
+                                              float tb, Emit &&emit, int *status = nullptr) {
   const Packet &P = sh.pk;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -219,6 +219,7 @@ __device__ __forceinline__ bool traverse_tile(SH &sh, const Node *__restrict__ n
       sp -= take;
       int node = lane < take ? sh.stack[sp + lane] : -1;
       __syncwarp();
+      if (node >= 0 && !MVP_IN_BOUNDS(node < 2 * n_prims - 1, status)) node = -1;
       bool pass = false, leaf = false;
       int l = 0, r = 0;
       if (node >= 0) {
@@ -234,7 +235,8 @@ __device__ __forceinline__ bool traverse_tile(SH &sh, const Node *__restrict__ n
       unsigned minner = __ballot_sync(FULL, pass && !leaf);
       int nl = __popc(mleaf), ni = __popc(minner);
       if (sp + 2 * ni > STACK) return false;
-      if (pass && leaf) sh.cand[nc + __popc(mleaf & lt)] = -1 - l;
+      if (pass && leaf)
+        sh.cand[nc + __popc(mleaf & lt)] = MVP_IN_BOUNDS(-1 - l >= 0 && -1 - l < n_prims, status) ? -1 - l : 0;
       if (pass && !leaf) {
         int pos = sp + 2 * __popc(minner & lt);
         sh.stack[pos] = r;
@@ -286,7 +288,7 @@ __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__r
                                             const Pose *__restrict__ pose, const Xform *__restrict__ xf,
                                             const char *payload, int64_t prim_bytes, int n_prims,
                                             const LaneRay &L, int lane_last, float t_near, float t_far, float dt,
-                                            int n_steps, int w0, int w1, int skip = 0) {
+                                            int n_steps, int w0, int w1, int skip = 0, int *status = nullptr) {
   const int lane = threadIdx.x & 31;
   float ta = sample_t(t_near, dt, w0);
   float tb = sample_t(t_near, dt, w1 - 1);
@@ -374,7 +376,7 @@ __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__r
     }
     return true;
   };
-  bool ok = traverse_tile(sh, nodes, n_prims, ta - slack, tb + slack, emit);
+  bool ok = traverse_tile(sh, nodes, n_prims, ta - slack, tb + slack, emit, status);
   __syncwarp();
   if (!ok && !full) return WINDOW_STACK;
   // the entries' march transforms and payload pointers, loaded in parallel
