@@ -119,12 +119,15 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def _frame_runner(cfg: str, seed: int, dtype: str, want_bwd: bool, torch, T, synthetic, sequential=False):
+def _frame_runner(cfg: str, seed: int, dtype: str, want_bwd: bool, torch, T, synthetic, sequential=False,
+                  schedule=True):
     """Set up a workload on the device; returns (step(), n_rays, info). sequential:
-    blend each ray's saturating sample in BVH order (MVP_BLEND_SEQUENTIAL)."""
+    blend each ray's saturating sample in BVH order (MVP_BLEND_SEQUENTIAL); schedule:
+    the library's cost-ordered tile schedule (off: the plain tile order)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     scene, rays, extra = synthetic.make_config(cfg, seed)
     ctx = T.Context(dev.index)
+    ctx.set_tile_schedule(schedule)
     t = torch.from_numpy(scene.t).to(dev)
     q = torch.from_numpy(scene.q).to(dev)
     s = torch.from_numpy(scene.s).to(dev)
@@ -335,6 +338,45 @@ def _ncu_record(kernel_key: str) -> dict:
     except Exception:
         return {}
     return {}
+
+
+def _orbit(torch, T, synthetic, args, flush, n_views=8, deg=0.5):
+    """The paper frame seen by a camera that orbits the avatar by `deg` degrees per
+    frame (rays made on the device per view beforehand), so every frame's tile
+    schedule comes from the previous, different view: the rate with the schedule and
+    with the plain tile order."""
+    out = {"views": n_views, "deg_per_frame": deg, "workload": WORKLOAD}
+    for sched in (True, False):
+        st, nr, inf = _frame_runner(WORKLOAD, 0, "f32", False, torch, T, synthetic, schedule=sched)
+        r = inf["rays"]
+        cam = r.cameras[0]
+        W, H = r.width, r.height
+        eye0 = np.asarray(cam.eye, np.float64)
+        rs = []
+        keep = []
+        for v in range(n_views):
+            a = np.deg2rad(deg * v)
+            rot = np.array([[np.cos(a), 0, np.sin(a)], [0, 1, 0], [-np.sin(a), 0, np.cos(a)]])
+            c = synthetic.look_at_camera(rot @ eye0, W, H, cam.focal)
+            o, d = T.camera_rays(inf["ctx"], c.matrix34(), cam.focal, W, H)
+            keep.append((o, d))
+            rs.append(T.rays_struct(o, d, t_near=r.t_near, t_far=r.t_far, dt=r.dt, width=W, height=H))
+        frame = [0]
+
+        def step():
+            inf["bvh"].build(inf["prims"])
+            T.raymarch_fwd(inf["ctx"], inf["prims"], inf["bvh"], rs[frame[0] % n_views], out=inf["out"])
+            frame[0] += 1
+
+        d = _time_steps(torch, step, args.steps, args.warmup, flush)
+        inf["ctx"].sync()
+        m = float(np.mean(d))
+        out["value_scheduled" if sched else "value_plain_order"] = round(nr / (m * 1e-3) / 1e6, 3)
+        out["ms_scheduled" if sched else "ms_plain_order"] = round(m, 4)
+        del st, inf, keep, rs
+        torch.cuda.empty_cache()
+    out["unit"] = "Mrays/s"
+    return out
 
 
 def _sequential_blend(torch, T, synthetic, args, flush):
@@ -677,8 +719,9 @@ def run_gpu(args):
                              if ncu.get("dram_bytes_per_launch") and peaks.get("hbm_gbs") else None),
                 "hbm_peak_GBps": peaks.get("hbm_gbs"), "hbm_peak_kind": peak_kind}
     # BVH: primitives + one-block sort (n <= 8192) or bounds, primitives and 4 radix
-    # passes of 3 kernels; then hierarchy, refit; then the march
-    launches_per_step = (2 if info["n_prims"] <= 8192 else 14) + 2 + 1
+    # passes of 3 kernels; then hierarchy, refit; then the march and the next frame's
+    # tile schedule
+    launches_per_step = (2 if info["n_prims"] <= 8192 else 14) + 2 + 1 + 1
     result = {"metric": METRIC, "value": round(value, 3), "unit": "Mrays/s", "n_gpus": ws, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; stands in for the paper's captures)",
@@ -699,19 +742,23 @@ def run_gpu(args):
 
     variants = {}
     if rank == 0 and not args.quick:
-        for name, cfg, dtype in (("fwd_bf16", WORKLOAD, "bf16"), ("fwd_f16", WORKLOAD, "f16"),
-                                 ("fwd_f32_512x32^3", "sweep_512x32^3_667x1024", "f32"),
-                                 ("fwd_f32_32768x8^3", "sweep_32768x8^3_667x1024", "f32"),
-                                 ("fwd_f32_dt0.01", "paper_4096x16^3_667x1024_dt0.01", "f32"),
-                                 ("fwd_f32_dt0.0025", "paper_4096x16^3_667x1024_dt0.0025", "f32"),
-                                 ("fwd_bf16_32768x8^3", "sweep_32768x8^3_667x1024", "bf16")):
-            st, nr, inf = _frame_runner(cfg, 0, dtype, False, torch, T, synthetic)
+        for name, cfg, dtype, sched in (("fwd_bf16", WORKLOAD, "bf16", True), ("fwd_f16", WORKLOAD, "f16", True),
+                                        ("fwd_f32_plain_tile_order", WORKLOAD, "f32", False),
+                                        ("fwd_f32_512x32^3", "sweep_512x32^3_667x1024", "f32", True),
+                                        ("fwd_f32_32768x8^3", "sweep_32768x8^3_667x1024", "f32", True),
+                                        ("fwd_f32_32768x8^3_plain_tile_order", "sweep_32768x8^3_667x1024", "f32",
+                                         False),
+                                        ("fwd_f32_dt0.01", "paper_4096x16^3_667x1024_dt0.01", "f32", True),
+                                        ("fwd_f32_dt0.0025", "paper_4096x16^3_667x1024_dt0.0025", "f32", True),
+                                        ("fwd_bf16_32768x8^3", "sweep_32768x8^3_667x1024", "bf16", True)):
+            st, nr, inf = _frame_runner(cfg, 0, dtype, False, torch, T, synthetic, schedule=sched)
             d = _time_steps(torch, st, args.steps, args.warmup, flush, time_march=True)
             inf["ctx"].sync()
             m = float(np.mean(d))
             mm = float(np.mean([a.elapsed_time(b) for a, b in inf["ev"]["march"]]))
             variants[name] = {"value": round(nr / (m * 1e-3) / 1e6, 3), "unit": "Mrays/s", "ms_per_step": round(m, 4),
-                              "march_ms": round(mm, 4), "workload": cfg, "payload_dtype": dtype}
+                              "march_ms": round(mm, 4), "workload": cfg, "payload_dtype": dtype,
+                              "tile_schedule": "by last frame's cost" if sched else "plain order"}
             if name == "fwd_bf16":
                 # end to end with the payload streamed from the host as BF16 (half the bytes)
                 e = _e2e(torch, T, inf, max(20, args.steps), 3, payload_dtype="bf16")
@@ -719,6 +766,7 @@ def run_gpu(args):
             del st, inf
             torch.cuda.empty_cache()
         variants["fwd_f32_sequential"] = _sequential_blend(torch, T, synthetic, args, flush)
+        variants["orbiting_camera"] = _orbit(torch, T, synthetic, args, flush)
         st, nr, inf = _frame_runner("diff_512x32^3_4x512x512", 0, "f32", True, torch, T, synthetic)
         d = _time_steps(torch, st, args.steps, args.warmup, flush)
         inf["ctx"].sync()

@@ -5,15 +5,36 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <string>
 
 #include "march.cuh"
 #include "pack.cuh"
 
+// The frame kernel's tile schedule: the warp tiles of the last frame sorted by the
+// cycles each took, so that the next frame of the same size starts its heaviest
+// tiles first (a tile started late on a busy GPU can otherwise outlast the rest of
+// the frame). Only one call at a time may touch the buffers: a call uses them if
+// the last call that did has finished or ran on the same stream, else it marches in
+// the plain tile order and leaves them alone. The schedule never changes a result:
+// each tile is still marched once, by one warp, in the same way.
+struct TileSched {
+  std::mutex mu;
+  bool enabled = true;
+  unsigned int *cost = nullptr;  // [cap] cycles per warp tile of the last frame
+  int *order = nullptr;          // [cap] the schedule derived from them
+  int64_t cap = 0;
+  int64_t tiles = -1;            // warp tiles `order` was made for (-1: none)
+  cudaEvent_t done = nullptr;    // after the last call that touched the buffers
+  cudaStream_t stream = nullptr; // ... and its stream
+  bool pending = false;
+};
+
 struct mvp_ctx {
   int device = 0;
   int *d_status = nullptr;  // device status word (STATUS_* bits)
+  TileSched sched;
 };
 
 struct mvp_bvh {
@@ -197,7 +218,18 @@ void mvp_ctx_destroy(mvp_ctx *ctx) {
   if (!ctx) return;
   DeviceGuard g(ctx->device);
   cudaFree(ctx->d_status);
+  if (ctx->sched.cost) cudaFree(ctx->sched.cost);
+  if (ctx->sched.order) cudaFree(ctx->sched.order);
+  if (ctx->sched.done) cudaEventDestroy(ctx->sched.done);
   delete ctx;
+}
+
+mvp_status mvp_ctx_set_tile_schedule(mvp_ctx *ctx, int32_t enable) {
+  if (!ctx) return fail(MVP_ERR_INVALID_ARG, "ctx is NULL");
+  std::lock_guard<std::mutex> lk(ctx->sched.mu);
+  ctx->sched.enabled = enable != 0;
+  ctx->sched.tiles = -1;  // start from the plain order
+  return ok();
 }
 
 int32_t mvp_bounds_checked(void) {
@@ -291,8 +323,51 @@ mvp_status mvp_raymarch_fwd(mvp_ctx *ctx, const mvp_prims *prims, const mvp_bvh 
   mvp::MarchArgs a = march_args(ctx, prims, bvh, rays, ns);
   a.out = out_rgba;
   a.saved = reinterpret_cast<mvp::Saved *>(saved);
-  cudaError_t e = mvp::launch_march(a, (cudaStream_t)stream);
+  TileSched &S = ctx->sched;
+  std::lock_guard<std::mutex> lk(S.mu);
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int64_t nt = a.geom.n_warp_tiles;
+  bool use = S.enabled && nt <= 0x7fffffff;
+  if (use && S.pending && S.stream != st) {
+    const cudaError_t q = cudaEventQuery(S.done);
+    if (q == cudaErrorNotReady) cudaGetLastError();  // not an error: the last scheduled call still runs
+    use = q == cudaSuccess;
+  }
+  if (use && nt > S.cap) {  // grow (cudaFree waits for work that may still use the old buffers)
+    if (S.cost) cudaFree(S.cost);
+    if (S.order) cudaFree(S.order);
+    S.cost = nullptr;
+    S.order = nullptr;
+    S.cap = 0;
+    S.tiles = -1;
+    if (cudaMalloc(&S.cost, (size_t)nt * sizeof(unsigned int)) != cudaSuccess ||
+        cudaMalloc(&S.order, (size_t)nt * sizeof(int)) != cudaSuccess ||
+        cudaMemset(S.cost, 0, (size_t)nt * sizeof(unsigned int)) != cudaSuccess ||
+        (!S.done && cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming) != cudaSuccess)) {
+      cudaGetLastError();
+      if (S.cost) cudaFree(S.cost);
+      if (S.order) cudaFree(S.order);
+      S.cost = nullptr;
+      S.order = nullptr;
+      use = false;  // no schedule: the plain order
+    } else {
+      S.cap = nt;
+    }
+  }
+  if (use) {
+    a.order = S.tiles == nt ? S.order : nullptr;
+    a.cost = S.cost;
+  }
+  cudaError_t e = mvp::launch_march(a, st);
   if (e != cudaSuccess) return cuda_fail(e, "march launch");
+  if (use) {
+    e = mvp::launch_tile_order(S.cost, nt, S.order, st);
+    if (e == cudaSuccess) e = cudaEventRecord(S.done, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tile schedule");
+    S.tiles = nt;
+    S.stream = st;
+    S.pending = true;
+  }
   return ok();
 }
 

@@ -35,6 +35,11 @@ struct MarchArgs {
   Saved *saved;
   int32_t *n_eval;  // count variant when non-null
   int *status;
+  // tile schedule (frame kernel only): warp slot s marches tile order[s] (a
+  // permutation of the warp tiles) when order is set; cost[t] receives the clock
+  // cycles tile t took when cost is set
+  const int *order;
+  unsigned int *cost;
 };
 
 struct HitArgs {
@@ -62,6 +67,9 @@ struct BwdArgs {
 };
 
 cudaError_t launch_march(const MarchArgs &a, cudaStream_t st);
+// order = the n warp tiles by descending cost bucket (a permutation of 0..n-1,
+// whatever cost holds): the next frame's schedule, heaviest tiles first.
+cudaError_t launch_tile_order(const unsigned int *cost, int64_t n, int *order, cudaStream_t st);
 void record_error(const char *msg);
 int ctx_device(const mvp_ctx *ctx);
 cudaError_t launch_hits(const HitArgs &a, int64_t *counts, cudaStream_t st);

@@ -198,6 +198,7 @@ struct TileShared {
   int ek[CAP];
   int elo[CAP], ehi[CAP];
   uint32_t erng[CAP][32];
+  unsigned int clk;  // the frame kernel's tile start (clock), for its tile schedule
 };
 
 // Traverse the BVH for the packet over [ta, tb]. Candidate leaves (primitive ids)

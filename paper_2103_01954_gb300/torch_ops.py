@@ -73,6 +73,10 @@ class Context:
     def sync(self):
         B.check(B.lib().mvp_ctx_sync(self.handle, _stream()), "mvp_ctx_sync")
 
+    def set_tile_schedule(self, enable: bool):
+        """Heaviest tiles of the last frame first (default), or the plain tile order."""
+        B.check(B.lib().mvp_ctx_set_tile_schedule(self.handle, 1 if enable else 0), "mvp_ctx_set_tile_schedule")
+
     def close(self):
         if self.handle:
             B.lib().mvp_ctx_destroy(self.handle)

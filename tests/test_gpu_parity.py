@@ -394,3 +394,29 @@ def test_degenerate_poses_reported():
     assert ei.value.status == B.MVP_ERR_INVALID_ARG
     assert srv.register(*(torch.from_numpy(x).cuda() for x in (sc.t, sc.q, sc.s, sc.payload))) == 0
     srv.close()
+
+
+def test_tile_schedule_changes_no_result():
+    """The frame kernel's cost-ordered tile schedule (heaviest tiles of the last frame
+    first) and the plain order give the same image bit for bit, on one stream and when
+    calls alternate between two streams."""
+    sc, rays, _ = synthetic.make_config("small_4096x16^3_83x128", 1)
+    dv = Dev(sc, rays).build()
+    dv.ctx.set_tile_schedule(False)
+    plain, _ = dv.render()
+    dv.ctx.set_tile_schedule(True)
+    for _ in range(3):  # the first frame records costs, the next ones use them
+        out, _ = dv.render()
+        assert torch.equal(out, plain)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = []
+    for k in range(6):
+        with torch.cuda.stream(s1 if k % 2 else s2):
+            o, _ = T.raymarch_fwd(dv.ctx, dv.prims, dv.bvh, dv.rs)
+            outs.append(o)
+    torch.cuda.synchronize()
+    dv.ctx.sync()
+    for o in outs:
+        assert torch.equal(o, plain)
+    ref = oracle.render(sc, rays, F32M)["rgba"]
+    _check_image(plain.cpu().numpy(), ref, "tile schedule")
