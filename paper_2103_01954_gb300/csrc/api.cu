@@ -26,8 +26,10 @@ struct TileSched {
   int *order = nullptr;          // [cap] the schedule derived from them
   int64_t cap = 0;
   int64_t tiles = -1;            // warp tiles `order` was made for (-1: none)
-  cudaEvent_t done = nullptr;    // after the last call that touched the buffers
-  cudaStream_t stream = nullptr; // ... and its stream
+  cudaEvent_t done = nullptr;    // after the last call's schedule kernel (on `side`)
+  cudaEvent_t marched = nullptr; // after that call's march (on its stream)
+  cudaStream_t side = nullptr;   // the schedule kernel runs here, beside the caller's next work
+  cudaStream_t stream = nullptr; // the stream of the last call that touched the buffers
   bool pending = false;
 };
 
@@ -221,6 +223,8 @@ void mvp_ctx_destroy(mvp_ctx *ctx) {
   if (ctx->sched.cost) cudaFree(ctx->sched.cost);
   if (ctx->sched.order) cudaFree(ctx->sched.order);
   if (ctx->sched.done) cudaEventDestroy(ctx->sched.done);
+  if (ctx->sched.marched) cudaEventDestroy(ctx->sched.marched);
+  if (ctx->sched.side) cudaStreamDestroy(ctx->sched.side);
   delete ctx;
 }
 
@@ -343,7 +347,9 @@ mvp_status mvp_raymarch_fwd(mvp_ctx *ctx, const mvp_prims *prims, const mvp_bvh 
     if (cudaMalloc(&S.cost, (size_t)nt * sizeof(unsigned int)) != cudaSuccess ||
         cudaMalloc(&S.order, (size_t)nt * sizeof(int)) != cudaSuccess ||
         cudaMemset(S.cost, 0, (size_t)nt * sizeof(unsigned int)) != cudaSuccess ||
-        (!S.done && cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming) != cudaSuccess)) {
+        (!S.done && cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming) != cudaSuccess) ||
+        (!S.marched && cudaEventCreateWithFlags(&S.marched, cudaEventDisableTiming) != cudaSuccess) ||
+        (!S.side && cudaStreamCreateWithFlags(&S.side, cudaStreamNonBlocking) != cudaSuccess)) {
       cudaGetLastError();
       if (S.cost) cudaFree(S.cost);
       if (S.order) cudaFree(S.order);
@@ -354,15 +360,21 @@ mvp_status mvp_raymarch_fwd(mvp_ctx *ctx, const mvp_prims *prims, const mvp_bvh 
       S.cap = nt;
     }
   }
+  cudaError_t e = cudaSuccess;
   if (use) {
     a.order = S.tiles == nt ? S.order : nullptr;
     a.cost = S.cost;
+    // the last schedule kernel (on the side stream) must be done with cost and order
+    if (S.pending) e = cudaStreamWaitEvent(st, S.done, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "tile schedule wait");
   }
-  cudaError_t e = mvp::launch_march(a, st);
+  e = mvp::launch_march(a, st);
   if (e != cudaSuccess) return cuda_fail(e, "march launch");
-  if (use) {
-    e = mvp::launch_tile_order(S.cost, nt, S.order, st);
-    if (e == cudaSuccess) e = cudaEventRecord(S.done, st);
+  if (use) {  // next frame's schedule, off the caller's stream (hidden behind its next BVH build)
+    e = cudaEventRecord(S.marched, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(S.side, S.marched, 0);
+    if (e == cudaSuccess) e = mvp::launch_tile_order(S.cost, nt, S.order, S.side);
+    if (e == cudaSuccess) e = cudaEventRecord(S.done, S.side);
     if (e != cudaSuccess) return cuda_fail(e, "tile schedule");
     S.tiles = nt;
     S.stream = st;
