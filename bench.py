@@ -197,16 +197,22 @@ def _time_steps(torch, step, steps, warmup, flush, time_march=False):
     return [a.elapsed_time(b) for a, b in durs]
 
 
-def _e2e(torch, T, info, steps, warmup, payload_dtype="f32"):
+def _e2e(torch, T, info, steps, warmup, payload_dtype="f32", rays_from="camera"):
     """The same frame through the C ABI from pinned host buffers: every step copies its
-    inputs (poses, payload, rays) host->device, builds the BVH, marches, and reads the
-    image back to pinned host memory. Frames are pipelined as a streaming renderer
-    would run them: frame k+1's inputs are copied on a copy stream (into the other of
-    two device buffer sets) while frame k renders, and each image is read back on a
-    third stream. The serial time (one stream, nothing overlapped) is reported beside."""
+    inputs (poses, payload) host->device, makes the camera's rays on the device
+    (rays_from="camera": the frame's input is the 3x4 camera and focal length, passed
+    by value) or copies precomputed rays from the host (rays_from="host"), builds the
+    BVH, marches, and reads the image back to pinned host memory. Frames are pipelined
+    as a streaming renderer would run them: frame k+1's inputs are copied on a copy
+    stream (into the other of two device buffer sets) while frame k renders, and each
+    image is read back on a third stream. The serial time (one stream, nothing
+    overlapped) is reported beside."""
     scene, rays = info["host"]
     dev = torch.device("cuda", torch.cuda.current_device())
-    hs = [torch.from_numpy(a).pin_memory() for a in (scene.t, scene.q, scene.s, scene.payload, rays.o, rays.d)]
+    cam = rays.cameras[0] if rays_from == "camera" else None
+    c2w = cam.matrix34() if cam else None
+    arrays = (scene.t, scene.q, scene.s, scene.payload) + (() if cam else (rays.o, rays.d))
+    hs = [torch.from_numpy(a).pin_memory() for a in arrays]
     if payload_dtype != "f32":
         # the host holds the payload in the reduced type (packed once by mvp_pack_payload)
         tdt = {"bf16": torch.bfloat16, "f16": torch.float16}[payload_dtype]
@@ -214,6 +220,8 @@ def _e2e(torch, T, info, steps, warmup, payload_dtype="f32"):
     sets = []
     for _ in range(2):
         ds = [torch.empty(h.shape, dtype=h.dtype, device=dev) for h in hs]
+        if cam:  # the rays' device buffers, filled from the camera every frame
+            ds += [torch.empty((rays.n, 3), dtype=torch.float32, device=dev) for _ in range(2)]
         prims = T.prims_struct(ds[0], ds[1], ds[2], ds[3])
         rs = T.rays_struct(ds[4], ds[5], t_near=rays.t_near, t_far=rays.t_far, dt=rays.dt, width=rays.width,
                            height=rays.height)
@@ -237,6 +245,8 @@ def _e2e(torch, T, info, steps, warmup, payload_dtype="f32"):
             st["copied"].record(copy_s)
         comp.wait_event(st["copied"])
         comp.wait_event(st["read"])  # the set's previous image has been read back
+        if cam:
+            T.camera_rays(ctx, c2w, cam.focal, rays.width, rays.height, out=(st["ds"][4], st["ds"][5]))
         bvh.build(st["prims"])
         T.raymarch_fwd(ctx, st["prims"], bvh, st["rs"], out=st["out"])
         st["rendered"].record(comp)
@@ -249,6 +259,8 @@ def _e2e(torch, T, info, steps, warmup, payload_dtype="f32"):
         st = sets[0]
         for h, d in zip(hs, st["ds"]):
             d.copy_(h, non_blocking=True)
+        if cam:
+            T.camera_rays(ctx, c2w, cam.focal, rays.width, rays.height, out=(st["ds"][4], st["ds"][5]))
         bvh.build(st["prims"])
         T.raymarch_fwd(ctx, st["prims"], bvh, st["rs"], out=st["out"])
         st["hout"].copy_(st["out"], non_blocking=True)
@@ -272,21 +284,28 @@ def _e2e(torch, T, info, steps, warmup, payload_dtype="f32"):
         serial_step()
     ms_serial = timed(lambda k: serial_step(), steps)
     ctx.sync()
-    # the streamed frames must equal the frame rendered from the resident inputs
-    # (of the same payload type)
+    # the streamed frames must equal the frame rendered from the resident inputs (of
+    # the same payload type; with the camera's rays when the frame makes its own)
     bvh.build(info["prims"])
-    T.raymarch_fwd(ctx, info["prims"], bvh, info["rs"], out=info["out"])
+    rs_ref = info["rs"]
+    if cam:
+        o, d = T.camera_rays(ctx, c2w, cam.focal, rays.width, rays.height)
+        rs_ref = T.rays_struct(o, d, t_near=rays.t_near, t_far=rays.t_far, dt=rays.dt, width=rays.width,
+                               height=rays.height)
+    T.raymarch_fwd(ctx, info["prims"], bvh, rs_ref, out=info["out"])
     ctx.sync()
     ref = info["out"].cpu()
     same = all(torch.equal(st["hout"], ref) for st in sets)
-    h2d = sum(h.numel() * h.element_size() for h in hs)
+    h2d = sum(h.numel() * h.element_size() for h in hs) + (13 * 4 if cam else 0)  # + camera and focal
     d2h = rays.n * 4 * 4
     return {"value": rays.n / (ms * 1e-3) / 1e6, "unit": "Mrays/s", "ms_per_step": ms, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "serial_ms_per_step": ms_serial,
             "serial_value": rays.n / (ms_serial * 1e-3) / 1e6,
             "pipeline": "frame k+1's inputs copied (copy stream, second buffer set) while frame k renders; "
                         "images read back on a third stream; every copy inside the timed region",
-            "payload_dtype": payload_dtype, "image_matches_resident_frame": bool(same)}
+            "payload_dtype": payload_dtype, "image_matches_resident_frame": bool(same),
+            "rays": "made on the device from the frame's camera (48 + 4 bytes in)" if cam
+            else "copied from the host every frame"}
 
 
 def _cpu_baseline(seconds: float = 15.0):
@@ -737,6 +756,7 @@ def run_gpu(args):
         dist.barrier()
     if rank == 0 and not args.quick:
         result["e2e"] = _e2e(torch, T, info, max(20, args.steps), 3)
+        result["e2e_rays_from_host"] = _e2e(torch, T, info, max(20, args.steps), 3, rays_from="host")
     del info, step
     torch.cuda.empty_cache()
 

@@ -244,10 +244,17 @@ def volume_prior(ctx: Context, s: torch.Tensor, lam: float = 0.01, g_s: torch.Te
     return loss, g_s
 
 
-def camera_rays(ctx: Context, c2w, focal: float, width: int, height: int):
+def camera_rays(ctx: Context, c2w, focal: float, width: int, height: int, out=None):
+    """mvp_camera_rays: (o, d) [width * height, 3] of a pinhole camera; out = (o, d)
+    writes into given tensors."""
     dev = torch.device("cuda", ctx.device)
-    o = torch.empty((width * height, 3), dtype=torch.float32, device=dev)
-    d = torch.empty((width * height, 3), dtype=torch.float32, device=dev)
+    if out is not None:
+        o, d = out
+        _need(o, "o", torch.float32, (3,))
+        _need(d, "d", torch.float32, (3,))
+    else:
+        o = torch.empty((width * height, 3), dtype=torch.float32, device=dev)
+        d = torch.empty((width * height, 3), dtype=torch.float32, device=dev)
     m = (ctypes.c_float * 12)(*[float(v) for v in list(c2w.reshape(-1))])
     B.check(B.lib().mvp_camera_rays(ctx.handle, m, float(focal), width, height, _ptr(o), _ptr(d), _stream()),
             "mvp_camera_rays")
