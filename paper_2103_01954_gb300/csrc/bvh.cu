@@ -306,7 +306,8 @@ constexpr int SORT1_BITS = 10, SORT1_BINS = 1 << SORT1_BITS;
 constexpr size_t SORT1_SMEM = sizeof(int) * (size_t)(SORT1_THREADS / 32) * SORT1_BINS;
 constexpr int SORT1_BUCKET_BITS = 13, SORT1_BUCKETS = 1 << SORT1_BUCKET_BITS;
 constexpr int SORT1_BUCKET_MAX = 64;  // largest bucket the insertion sort takes
-static_assert(2 * SORT1_BUCKETS * sizeof(int) <= SORT1_SMEM, "bucket arrays live in the digit-count area");
+static_assert((2 * SORT1_BUCKETS + 2 * BVH_SORT1_N) * sizeof(int) <= SORT1_SMEM,
+              "bucket arrays and the staged keys live in the digit-count area");
 static_assert(SORT1_BUCKETS % SORT1_THREADS == 0, "whole buckets per thread");
 
 __global__ void __launch_bounds__(SORT1_THREADS) k_sort_one(const float *__restrict__ t, int n,
@@ -341,6 +342,8 @@ __global__ void __launch_bounds__(SORT1_THREADS) k_sort_one(const float *__restr
   {
     int *cnt = reinterpret_cast<int *>(smem_raw);  // [8192] counts, then bucket starts
     int *cur = cnt + SORT1_BUCKETS;                // [8192] scatter cursors
+    uint32_t *sk = reinterpret_cast<uint32_t *>(cur + SORT1_BUCKETS);  // [n] keys, bucketed, then sorted
+    int *sv = reinterpret_cast<int *>(sk + BVH_SORT1_N);                // [n] their primitive indices
     for (int b = tid; b < SORT1_BUCKETS; b += SORT1_THREADS) cnt[b] = 0;
     __syncthreads();
     for (int k = tid; k < n; k += SORT1_THREADS) atomicAdd(&cnt[kb[k] >> (30 - SORT1_BUCKET_BITS)], 1);
@@ -390,28 +393,34 @@ __global__ void __launch_bounds__(SORT1_THREADS) k_sort_one(const float *__restr
         run += c;
       }
       __syncthreads();
+      // scatter into shared memory, sort each bucket there, then write out coalesced
       for (int k = tid; k < n; k += SORT1_THREADS) {
         const uint32_t key = kb[k];
         const int pos = atomicAdd(&cur[key >> (30 - SORT1_BUCKET_BITS)], 1);
-        ka[pos] = key;
-        va[pos] = k;
+        sk[pos] = key;
+        sv[pos] = k;
       }
       __syncthreads();
       for (int b = tid; b < SORT1_BUCKETS; b += SORT1_THREADS) {
         const int s0 = cnt[b], e0 = b + 1 < SORT1_BUCKETS ? cnt[b + 1] : n;
         for (int x = s0 + 1; x < e0; ++x) {
-          const uint32_t kx = ka[x];
-          const int vx = va[x];
+          const uint32_t kx = sk[x];
+          const int vx = sv[x];
           const uint64_t cx = ((uint64_t)kx << 32) | (uint32_t)vx;
           int y = x - 1;
-          while (y >= s0 && (((uint64_t)ka[y] << 32) | (uint32_t)va[y]) > cx) {
-            ka[y + 1] = ka[y];
-            va[y + 1] = va[y];
+          while (y >= s0 && (((uint64_t)sk[y] << 32) | (uint32_t)sv[y]) > cx) {
+            sk[y + 1] = sk[y];
+            sv[y + 1] = sv[y];
             --y;
           }
-          ka[y + 1] = kx;
-          va[y + 1] = vx;
+          sk[y + 1] = kx;
+          sv[y + 1] = vx;
         }
+      }
+      __syncthreads();
+      for (int k = tid; k < n; k += SORT1_THREADS) {
+        ka[k] = sk[k];
+        va[k] = sv[k];
       }
       return;
     }
