@@ -186,13 +186,15 @@ MVP_API mvp_status mvp_hitlists(mvp_ctx *ctx, const mvp_prims *prims, const mvp_
 /* ------------------------------------------ forward march (Sec. 3.2.2) */
 /* Bytes of per-ray state the forward saves for the adjoint (24 per ray). */
 MVP_API size_t mvp_saved_bytes(int64_t n_rays);
-/* The frame kernel's tile schedule (on by default): each mvp_raymarch_fwd records
- * how long each warp tile took and the next call with the same number of tiles
- * starts the heaviest tiles first, so that no expensive tile (rays grazing many
- * primitives) starts late and outlasts the frame. It changes no result. The first
- * call at a new, larger tile count allocates its buffers (cudaMalloc). Calls on
- * other streams that overlap the last scheduled one march in the plain order.
- * enable = 0 always marches in the plain order. */
+/* The tile schedule of the frame kernel and of the adjoint (on by default): each
+ * mvp_raymarch_fwd (and, separately, each mvp_raymarch_bwd) records how long each
+ * warp tile took and the next call with the same number of tiles starts the
+ * heaviest tiles first, so that no expensive tile (rays grazing many primitives)
+ * starts late and outlasts the frame. It changes no image (the adjoint's gradients
+ * only by the order of their float reductions). The first call at a new, larger
+ * tile count allocates its buffers (cudaMalloc). Calls on other streams that overlap
+ * the last scheduled one use the plain order. enable = 0 always uses the plain
+ * order. */
 MVP_API mvp_status mvp_ctx_set_tile_schedule(mvp_ctx *ctx, int32_t enable);
 /* Render: out_rgba [n][4] float32 device = (I + (1 - A) bg, A). `saved`
  * (device, mvp_saved_bytes(n) bytes, nullable) receives the per-ray state the

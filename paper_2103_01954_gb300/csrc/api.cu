@@ -36,7 +36,8 @@ struct TileSched {
 struct mvp_ctx {
   int device = 0;
   int *d_status = nullptr;  // device status word (STATUS_* bits)
-  TileSched sched;
+  TileSched sched;          // the frame kernel's
+  TileSched sched_bwd;      // the adjoint's
 };
 
 struct mvp_bvh {
@@ -112,6 +113,73 @@ mvp_status check_bvh(const mvp_bvh *bvh, const mvp_prims *p) {
     return fail(MVP_ERR_INVALID_ARG, "bvh was built for n=%d M=%d, prims have n=%d M=%d", bvh->b.n, bvh->b.M, p->n,
                 p->M);
   return ok();
+}
+
+// Tile schedule of one kernel launch (the caller holds S.mu): sched_begin decides
+// whether this call may use the buffers (the last call that touched them has
+// finished or ran on this stream), grows them if needed, points the launch at them
+// and makes the stream wait for the last schedule kernel; sched_end queues the
+// schedule kernel for the next call on the side stream. The plain tile order is the
+// fallback whenever something is unavailable.
+bool sched_begin(TileSched &S, mvp::MarchArgs &a, cudaStream_t st, cudaError_t &e) {
+  e = cudaSuccess;
+  const int64_t nt = a.geom.n_warp_tiles;
+  bool use = S.enabled && nt <= 0x7fffffff;
+  if (use && S.pending && S.stream != st) {
+    const cudaError_t q = cudaEventQuery(S.done);
+    if (q == cudaErrorNotReady) cudaGetLastError();  // not an error: the last scheduled call still runs
+    use = q == cudaSuccess;
+  }
+  if (use && nt > S.cap) {  // grow (cudaFree waits for work that may still use the old buffers)
+    if (S.cost) cudaFree(S.cost);
+    if (S.order) cudaFree(S.order);
+    S.cost = nullptr;
+    S.order = nullptr;
+    S.cap = 0;
+    S.tiles = -1;
+    if (cudaMalloc(&S.cost, (size_t)nt * sizeof(unsigned int)) != cudaSuccess ||
+        cudaMalloc(&S.order, (size_t)nt * sizeof(int)) != cudaSuccess ||
+        cudaMemset(S.cost, 0, (size_t)nt * sizeof(unsigned int)) != cudaSuccess ||
+        (!S.done && cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming) != cudaSuccess) ||
+        (!S.marched && cudaEventCreateWithFlags(&S.marched, cudaEventDisableTiming) != cudaSuccess) ||
+        (!S.side && cudaStreamCreateWithFlags(&S.side, cudaStreamNonBlocking) != cudaSuccess)) {
+      cudaGetLastError();
+      if (S.cost) cudaFree(S.cost);
+      if (S.order) cudaFree(S.order);
+      S.cost = nullptr;
+      S.order = nullptr;
+      use = false;
+    } else {
+      S.cap = nt;
+    }
+  }
+  if (use) {
+    a.order = S.tiles == nt ? S.order : nullptr;
+    a.cost = S.cost;
+    if (S.pending) e = cudaStreamWaitEvent(st, S.done, 0);  // the last schedule kernel is done with them
+  }
+  return use;
+}
+
+cudaError_t sched_end(TileSched &S, int64_t nt, cudaStream_t st) {
+  cudaError_t e = cudaEventRecord(S.marched, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(S.side, S.marched, 0);
+  if (e == cudaSuccess) e = mvp::launch_tile_order(S.cost, nt, S.order, S.side);
+  if (e == cudaSuccess) e = cudaEventRecord(S.done, S.side);
+  if (e == cudaSuccess) {
+    S.tiles = nt;
+    S.stream = st;
+    S.pending = true;
+  }
+  return e;
+}
+
+void sched_free(TileSched &S) {
+  if (S.cost) cudaFree(S.cost);
+  if (S.order) cudaFree(S.order);
+  if (S.done) cudaEventDestroy(S.done);
+  if (S.marched) cudaEventDestroy(S.marched);
+  if (S.side) cudaStreamDestroy(S.side);
 }
 
 mvp::MarchArgs march_args(mvp_ctx *ctx, const mvp_prims *p, const mvp_bvh *bvh, const mvp_rays *r, int64_t ns) {
@@ -220,19 +288,18 @@ void mvp_ctx_destroy(mvp_ctx *ctx) {
   if (!ctx) return;
   DeviceGuard g(ctx->device);
   cudaFree(ctx->d_status);
-  if (ctx->sched.cost) cudaFree(ctx->sched.cost);
-  if (ctx->sched.order) cudaFree(ctx->sched.order);
-  if (ctx->sched.done) cudaEventDestroy(ctx->sched.done);
-  if (ctx->sched.marched) cudaEventDestroy(ctx->sched.marched);
-  if (ctx->sched.side) cudaStreamDestroy(ctx->sched.side);
+  sched_free(ctx->sched);
+  sched_free(ctx->sched_bwd);
   delete ctx;
 }
 
 mvp_status mvp_ctx_set_tile_schedule(mvp_ctx *ctx, int32_t enable) {
   if (!ctx) return fail(MVP_ERR_INVALID_ARG, "ctx is NULL");
-  std::lock_guard<std::mutex> lk(ctx->sched.mu);
-  ctx->sched.enabled = enable != 0;
-  ctx->sched.tiles = -1;  // start from the plain order
+  for (TileSched *S : {&ctx->sched, &ctx->sched_bwd}) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->enabled = enable != 0;
+    S->tiles = -1;  // start from the plain order
+  }
   return ok();
 }
 
@@ -330,56 +397,12 @@ mvp_status mvp_raymarch_fwd(mvp_ctx *ctx, const mvp_prims *prims, const mvp_bvh 
   TileSched &S = ctx->sched;
   std::lock_guard<std::mutex> lk(S.mu);
   const cudaStream_t st = (cudaStream_t)stream;
-  const int64_t nt = a.geom.n_warp_tiles;
-  bool use = S.enabled && nt <= 0x7fffffff;
-  if (use && S.pending && S.stream != st) {
-    const cudaError_t q = cudaEventQuery(S.done);
-    if (q == cudaErrorNotReady) cudaGetLastError();  // not an error: the last scheduled call still runs
-    use = q == cudaSuccess;
-  }
-  if (use && nt > S.cap) {  // grow (cudaFree waits for work that may still use the old buffers)
-    if (S.cost) cudaFree(S.cost);
-    if (S.order) cudaFree(S.order);
-    S.cost = nullptr;
-    S.order = nullptr;
-    S.cap = 0;
-    S.tiles = -1;
-    if (cudaMalloc(&S.cost, (size_t)nt * sizeof(unsigned int)) != cudaSuccess ||
-        cudaMalloc(&S.order, (size_t)nt * sizeof(int)) != cudaSuccess ||
-        cudaMemset(S.cost, 0, (size_t)nt * sizeof(unsigned int)) != cudaSuccess ||
-        (!S.done && cudaEventCreateWithFlags(&S.done, cudaEventDisableTiming) != cudaSuccess) ||
-        (!S.marched && cudaEventCreateWithFlags(&S.marched, cudaEventDisableTiming) != cudaSuccess) ||
-        (!S.side && cudaStreamCreateWithFlags(&S.side, cudaStreamNonBlocking) != cudaSuccess)) {
-      cudaGetLastError();
-      if (S.cost) cudaFree(S.cost);
-      if (S.order) cudaFree(S.order);
-      S.cost = nullptr;
-      S.order = nullptr;
-      use = false;  // no schedule: the plain order
-    } else {
-      S.cap = nt;
-    }
-  }
   cudaError_t e = cudaSuccess;
-  if (use) {
-    a.order = S.tiles == nt ? S.order : nullptr;
-    a.cost = S.cost;
-    // the last schedule kernel (on the side stream) must be done with cost and order
-    if (S.pending) e = cudaStreamWaitEvent(st, S.done, 0);
-    if (e != cudaSuccess) return cuda_fail(e, "tile schedule wait");
-  }
+  const bool use = sched_begin(S, a, st, e);
+  if (e != cudaSuccess) return cuda_fail(e, "tile schedule wait");
   e = mvp::launch_march(a, st);
   if (e != cudaSuccess) return cuda_fail(e, "march launch");
-  if (use) {  // next frame's schedule, off the caller's stream (hidden behind its next BVH build)
-    e = cudaEventRecord(S.marched, st);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(S.side, S.marched, 0);
-    if (e == cudaSuccess) e = mvp::launch_tile_order(S.cost, nt, S.order, S.side);
-    if (e == cudaSuccess) e = cudaEventRecord(S.done, S.side);
-    if (e != cudaSuccess) return cuda_fail(e, "tile schedule");
-    S.tiles = nt;
-    S.stream = st;
-    S.pending = true;
-  }
+  if (use && (e = sched_end(S, a.geom.n_warp_tiles, st)) != cudaSuccess) return cuda_fail(e, "tile schedule");
   return ok();
 }
 
@@ -424,8 +447,15 @@ mvp_status mvp_raymarch_bwd(mvp_ctx *ctx, const mvp_prims *prims, mvp_bvh *bvh, 
   b.grad = grad_rgba;
   b.g_payload = g_payload;
   b.gmc = pose ? bvh->b.gmc : nullptr;
-  cudaError_t e = mvp::launch_backward(b, prims->t, prims->q, prims->s, g_t, g_q, g_s, (cudaStream_t)stream);
+  TileSched &S = ctx->sched_bwd;
+  std::lock_guard<std::mutex> lk(S.mu);
+  const cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  const bool use = sched_begin(S, b.m, st, e);
+  if (e != cudaSuccess) return cuda_fail(e, "tile schedule wait");
+  e = mvp::launch_backward(b, prims->t, prims->q, prims->s, g_t, g_q, g_s, st);
   if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+  if (use && (e = sched_end(S, b.m.geom.n_warp_tiles, st)) != cudaSuccess) return cuda_fail(e, "tile schedule");
   return ok();
 }
 

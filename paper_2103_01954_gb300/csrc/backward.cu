@@ -18,18 +18,12 @@
 
 namespace mvp {
 
+// The adjoint of one warp tile whose lane ray is L.
 template <int DT, int CAP, int MT>
-__global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs &b, const LaneRay &L) {
   const MarchArgs &a = b.m;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  TileShared<CAP> &sh = reinterpret_cast<TileShared<CAP> *>(smem_raw)[warp];
-  const int64_t wt = (int64_t)blockIdx.x * TILE_WARPS + warp;
-  if (wt >= a.geom.n_warp_tiles) return;
-  LaneRay L;
-  load_lane_ray(L, a.o, a.d, tile_ray(a.geom, wt, lane));
+  const int lane = threadIdx.x & 31;
   const bool valid = L.r >= 0;
-  if (__ballot_sync(FULL, valid) == 0) return;
 
   // per-ray adjoint constants
   int i_last = -1, i_clamp = -1;
@@ -211,6 +205,39 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
     skip = 0;
     w0 = w1;
     wlen = min(a.n_steps, wlen * 2);
+  }
+}
+
+// The tile schedule as in the frame kernel (its own cost record: the adjoint's
+// expensive tiles are not quite the forward's).
+template <int DT, int CAP, int MT>
+__global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const MarchArgs &a = b.m;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  TileShared<CAP> &sh = reinterpret_cast<TileShared<CAP> *>(smem_raw)[warp];
+  const int64_t slot = (int64_t)blockIdx.x * TILE_WARPS + warp;
+  if (slot >= a.geom.n_warp_tiles) return;
+  int64_t wt = slot;
+  if (a.order) {
+    const int o = __ldg(a.order + slot);
+    if (o >= 0 && o < a.geom.n_warp_tiles) wt = o;
+  }
+  LaneRay L;
+  load_lane_ray(L, a.o, a.d, tile_ray(a.geom, wt, lane));
+  if (__ballot_sync(FULL, L.r >= 0) == 0) return;
+  if (lane == 0) sh.clk = (unsigned int)clock();
+  backward_tile<DT, CAP, MT>(sh, b, L);
+  if (a.cost) {
+    __syncwarp();
+    if (lane == 0) {
+      int64_t t = slot;
+      if (a.order) {
+        const int o = __ldg(a.order + slot);
+        if (o >= 0 && o < a.geom.n_warp_tiles) t = o;
+      }
+      a.cost[t] = (unsigned int)clock() - sh.clk;
+    }
   }
 }
 
