@@ -110,7 +110,8 @@ typedef struct mvp_rays {
  * one in BVH order (the order of their leaves: ascending (morton << 32 | k)), as the
  * paper describes for overlapping primitives (Sec. 3.2.2), instead of summing them and
  * clamping once. Every other sample is unaffected (the two rules agree wherever T
- * stays below 1). Forward only: mvp_raymarch_bwd rejects it. */
+ * stays below 1). mvp_raymarch_bwd differentiates the rule the forward applied (pass
+ * the same flags to both). */
 #define MVP_BLEND_SEQUENTIAL 1
 /* mvp_rays.flags: the background composite read literally as I~ = A I + (1 - A) B
  * (Sec. 3.1.4) instead of I~ = I + (1 - A) B, which treats the marched I as already
@@ -184,7 +185,7 @@ MVP_API mvp_status mvp_hitlists(mvp_ctx *ctx, const mvp_prims *prims, const mvp_
                         int64_t *n_hits, mvp_stream stream);
 
 /* ------------------------------------------ forward march (Sec. 3.2.2) */
-/* Bytes of per-ray state the forward saves for the adjoint (24 per ray). */
+/* Bytes of per-ray state the forward saves for the adjoint (32 per ray). */
 MVP_API size_t mvp_saved_bytes(int64_t n_rays);
 /* The tile schedule of the frame kernel and of the adjoint (on by default): each
  * mvp_raymarch_fwd (and, separately, each mvp_raymarch_bwd) records how long each

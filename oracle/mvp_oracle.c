@@ -445,8 +445,10 @@ typedef struct {
   double rgb[3], T;
   int i_last;      /* last sample processed (the ray stops after it) */
   int i_clamp;     /* sample where w = 1 - T < a (saturation), or -1 */
-  double rho[3];   /* c/a at i_clamp */
-  double beta;     /* (1 - T)/a at i_clamp */
+  double rho[3];   /* c/a at i_clamp (sequential: the colour of the primitive whose weight was
+                    * clamped there, or 0 if none was) */
+  double beta;     /* (1 - T)/a at i_clamp (sequential: that primitive's weight) */
+  int seq_k;       /* sequential: the primitive clamped at i_clamp, or -1 */
   int64_t n_eval;  /* (sample, primitive) evaluations */
   int near_face;
 } ray_out_t;
@@ -482,6 +484,7 @@ static void march_ray(const scene_t *sc, const march_t *m, int64_t r, int mode, 
   res->i_clamp = -1;
   res->rho[0] = res->rho[1] = res->rho[2] = 0.0;
   res->beta = 0.0;
+  res->seq_k = -1;
   res->n_eval = 0;
   res->near_face = 0;
   int nk = pruned ? nc : sc->n;
@@ -536,11 +539,27 @@ static void march_ray(const scene_t *sc, const march_t *m, int64_t r, int mode, 
         while (y1 >= 0 && sc->rank[seq[y1].k] > sc->rank[cur.k]) { seq[y1 + 1] = seq[y1]; --y1; }
         seq[y1 + 1] = cur;
       }
+      res->rho[0] = res->rho[1] = res->rho[2] = 0.0;
+      res->beta = 0.0;
+      int last = -1; /* the last contributing primitive while none has been clamped */
       for (int e = 0; e < n_in && rem > 0.0; ++e) {
         double w = m->dt * seq[e].v[3];
-        if (w > rem) w = rem;
+        if (w >= rem) {  /* this primitive's weight is clamped to what is left */
+          w = rem;
+          res->seq_k = seq[e].k;
+          res->rho[0] = seq[e].v[0]; res->rho[1] = seq[e].v[1]; res->rho[2] = seq[e].v[2];
+          res->beta = w;
+          last = -2;
+        } else if (w > 0.0) {
+          last = e;
+        }
         I[0] += seq[e].v[0] * w; I[1] += seq[e].v[1] * w; I[2] += seq[e].v[2] * w;
         rem -= w;
+      }
+      if (last >= 0) { /* rounding left every weight below what was left: the last one */
+        res->seq_k = seq[last].k;
+        res->rho[0] = seq[last].v[0]; res->rho[1] = seq[last].v[1]; res->rho[2] = seq[last].v[2];
+        res->beta = m->dt * seq[last].v[3];
       }
       res->i_clamp = i;
       T = 1.0;
@@ -598,11 +617,14 @@ static int scene_rank(scene_t *sc) {
 }
 
 /* Render: out[r] = (I + (1 - A) bg, A) (R5); near_face, n_eval and the adjoint
- * state (i_last, i_clamp, rho, beta) are optional. Returns 0, or -1 on bad input. */
+ * state (i_last, i_clamp; beta: (1 - T)/a at i_clamp, or under the sequential rule the
+ * clamped primitive's weight; clamp_k: that primitive, -1 if none) are optional.
+ * Returns 0, or -1 on bad input. */
 int orc_render(int n, int M, const float *t, const float *q, const float *s, const float *payload,
                int64_t n_rays, const float *o, const float *d, float t_near, float t_far, float dt,
                float eps, const float *bg, int n_steps, int mode, int n_threads, double *out,
-               uint8_t *near_face, int64_t *n_eval, int32_t *i_last, int32_t *i_clamp) {
+               uint8_t *near_face, int64_t *n_eval, int32_t *i_last, int32_t *i_clamp, double *beta,
+               int32_t *clamp_k) {
   if (n < 0 || M < 2 || n_rays < 0 || !(dt > 0) || n_steps < 0) return -1;
   scene_t sc;
   if (scene_init(&sc, n, M, t, q, s, payload)) return -1;
@@ -630,6 +652,8 @@ int orc_render(int n, int M, const float *t, const float *q, const float *s, con
       if (n_eval) n_eval[r] = res.n_eval;
       if (i_last) i_last[r] = res.i_last;
       if (i_clamp) i_clamp[r] = res.i_clamp;
+      if (beta) beta[r] = res.beta;
+      if (clamp_k) clamp_k[r] = res.seq_k;
     }
     free(cands);
     free(seq);
@@ -680,10 +704,15 @@ int orc_backward(int n, int M, const float *t, const float *q, const float *s, c
                  float eps, const float *bg, int n_steps, int mode, int n_threads,
                  const double *grad_out, double *g_payload, double *g_t, double *g_q, double *g_s) {
   if (n < 0 || M < 2 || n_rays < 0 || !(dt > 0) || n_steps < 0) return -1;
-  if (mode & (ORC_SEQUENTIAL | ORC_LITERAL)) return -1; /* summed rule, premultiplied composite only */
+  if (mode & ORC_LITERAL) return -1; /* premultiplied composite only */
   scene_t sc;
   if (scene_init(&sc, n, M, t, q, s, payload)) return -1;
   march_t m = {o, d, t_near, t_far, dt, eps, {bg[0], bg[1], bg[2]}, n_steps};
+  const int sequential = (mode & ORC_SEQUENTIAL) != 0;
+  if (sequential && scene_rank(&sc)) {
+    scene_free(&sc);
+    return -1;
+  }
   double *gR = (double *)calloc(9 * (size_t)(n > 0 ? n : 1), sizeof(double));
   int pruned = mode & 1, f32m = (mode >> 1) & 1;
 #ifdef _OPENMP
@@ -692,10 +721,11 @@ int orc_backward(int n, int M, const float *t, const float *q, const float *s, c
 #pragma omp parallel
   {
     cand_t *cands = (cand_t *)malloc(sizeof(cand_t) * (size_t)(n > 0 ? n : 1));
+    seq_t *seqb = (seq_t *)malloc(sizeof(seq_t) * (size_t)(n > 0 ? n : 1));
 #pragma omp for schedule(dynamic, 16)
     for (int64_t r = 0; r < n_rays; ++r) {
       ray_out_t res;
-      march_ray(&sc, &m, r, mode & ~ORC_SEQUENTIAL, cands, NULL, &res);
+      march_ray(&sc, &m, r, mode, cands, seqb, &res);
       int nc = (pruned || f32m) ? ray_candidates(&sc, &m, r, cands) : 0;
       const double *go = grad_out + 4 * r;
       double gI[3] = {go[0], go[1], go[2]};
@@ -732,10 +762,28 @@ int orc_backward(int n, int M, const float *t, const float *q, const float *s, c
           double v[4], cw[8], dvdu[4][3];
           int64_t cidx[8];
           float u32[3];
+          /* sequential rule at the saturating sample S, with J the primitive whose weight was
+           * clamped (w_J = 1 - T - the weights before it): a primitive before J in BVH order
+           * adds dt alpha c and takes dt alpha from w_J, so it is differentiated like a
+           * sample before S (dL/da = -gI.c_J, dL/dc = gI); J adds w_J c_J and its alpha does
+           * not change I (dL/dalpha = 0, dL/dc = w_J gI); primitives after J add nothing.
+           * Samples before S see dL/da = -gI.c_J (through 1 - T); with no clamped primitive
+           * c_J = 0. */
+          int seq_role = 0; /* 0: summed rule; 1: before J; 2: J; 3: after J */
+          if (sequential && res.i_clamp >= 0 && i == res.i_clamp) {
+            if (res.seq_k < 0 || sc.rank[k] < sc.rank[res.seq_k]) seq_role = 1;
+            else seq_role = k == res.seq_k ? 2 : 3;
+          }
+          if (seq_role == 3) continue;
           if (f32m) voxel_coord_f32(sc.U32 + 12 * k, or_, dr, ti32, u32);
           trilinear(&sc, k, y, f32m ? u32 : NULL, v, cidx, cw, dvdu);
-          double galpha = dt * (ga + gc[0] * v[0] + gc[1] * v[1] + gc[2] * v[2]);
-          double gv[4] = {dt * v[3] * gc[0], dt * v[3] * gc[1], dt * v[3] * gc[2], galpha};
+          double ga_k = ga, gc_k[3] = {gc[0], gc[1], gc[2]};
+          if (seq_role == 1) { ga_k = -gIrho; gc_k[0] = gI[0]; gc_k[1] = gI[1]; gc_k[2] = gI[2]; }
+          double galpha = dt * (ga_k + gc_k[0] * v[0] + gc_k[1] * v[1] + gc_k[2] * v[2]);
+          double gv[4] = {dt * v[3] * gc_k[0], dt * v[3] * gc_k[1], dt * v[3] * gc_k[2], galpha};
+          if (seq_role == 2) {
+            gv[0] = res.beta * gI[0]; gv[1] = res.beta * gI[1]; gv[2] = res.beta * gI[2]; gv[3] = 0.0;
+          }
           double *GP = g_payload + (size_t)k * M * M * M * 4;
           for (int cn = 0; cn < 8; ++cn)
             for (int ch = 0; ch < 4; ++ch) {
@@ -768,6 +816,7 @@ int orc_backward(int n, int M, const float *t, const float *q, const float *s, c
       }
     }
     free(cands);
+    free(seqb);
   }
   for (int k = 0; k < n; ++k) {
     double gq4[4];

@@ -58,7 +58,7 @@ def _load():
     lib.orc_morton_keys.argtypes = [i32, P, P, P]
     lib.orc_radix_tree.argtypes = [i32, P, P, P]
     lib.orc_render.argtypes = [i32, i32, P, P, P, P, i64, P, P, f32, f32, f32, f32, P, i32, i32, i32,
-                               P, P, P, P, P]
+                               P, P, P, P, P, P, P]
     lib.orc_render.restype = i32
     lib.orc_backward.argtypes = [i32, i32, P, P, P, P, i64, P, P, f32, f32, f32, f32, P, i32, i32, i32,
                                  P, P, P, P, P]
@@ -146,7 +146,8 @@ def _march_args(scene, rays, n_steps=None):
 
 def render(scene, rays, mode: int = MODE_PRUNED | MEMBER_F32, n_threads: int = 0):
     """FP64 render. Returns dict with rgba [R,4] float64, near_face [R] bool,
-    n_eval [R] int64, i_last [R], i_clamp [R]."""
+    n_eval [R] int64, i_last [R], i_clamp [R], beta [R] (the adjoint's clamp weight),
+    clamp_k [R] (sequential rule: the primitive clamped at i_clamp, -1 if none)."""
     t, q, s, payload, o, d, bg, ns = _march_args(scene, rays)
     R = o.shape[0]
     out = np.zeros((R, 4), np.float64)
@@ -154,12 +155,15 @@ def render(scene, rays, mode: int = MODE_PRUNED | MEMBER_F32, n_threads: int = 0
     ne = np.zeros(R, np.int64)
     il = np.zeros(R, np.int32)
     ic = np.zeros(R, np.int32)
+    be = np.zeros(R, np.float64)
+    ck = np.zeros(R, np.int32)
     rc = _load().orc_render(t.shape[0], scene.M, _p(t), _p(q), _p(s), _p(payload), R, _p(o), _p(d),
                             rays.t_near, rays.t_far, rays.dt, rays.eps_early, _p(bg), ns, mode,
-                            n_threads, _p(out), _p(nf), _p(ne), _p(il), _p(ic))
+                            n_threads, _p(out), _p(nf), _p(ne), _p(il), _p(ic), _p(be), _p(ck))
     if rc != 0:
         raise ValueError("oracle render rejected its arguments")
-    return {"rgba": out, "near_face": nf.astype(bool), "n_eval": ne, "i_last": il, "i_clamp": ic}
+    return {"rgba": out, "near_face": nf.astype(bool), "n_eval": ne, "i_last": il, "i_clamp": ic, "beta": be,
+            "clamp_k": ck}
 
 
 def backward(scene, rays, grad_out, mode: int = MODE_PRUNED | MEMBER_F32, n_threads: int = 0):

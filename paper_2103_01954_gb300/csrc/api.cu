@@ -432,8 +432,6 @@ mvp_status mvp_raymarch_bwd(mvp_ctx *ctx, const mvp_prims *prims, mvp_bvh *bvh, 
   bool pose = g_t || g_q || g_s;
   if (pose && !(g_t && g_q && g_s)) return fail(MVP_ERR_INVALID_ARG, "g_t, g_q and g_s go together");
   if (rays->n > 0 && (!saved || !grad_rgba)) return fail(MVP_ERR_INVALID_ARG, "saved and grad_rgba are required");
-  if (rays->flags & MVP_BLEND_SEQUENTIAL)
-    return fail(MVP_ERR_INVALID_ARG, "the adjoint supports the summed blending rule only");
   if (rays->flags & MVP_COMPOSITE_LITERAL)
     return fail(MVP_ERR_INVALID_ARG, "the adjoint supports the premultiplied composite only");
   if (reinterpret_cast<uintptr_t>(g_payload) % 16 || reinterpret_cast<uintptr_t>(grad_rgba) % 16 ||

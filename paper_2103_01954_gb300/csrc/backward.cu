@@ -18,15 +18,16 @@
 
 namespace mvp {
 
-// The adjoint of one warp tile whose lane ray is L.
-template <int DT, int CAP, int MT>
+// The adjoint of one warp tile whose lane ray is L (SEQ: the forward blended the
+// saturating samples in BVH order).
+template <int DT, int CAP, int MT, bool SEQ>
 __device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs &b, const LaneRay &L) {
   const MarchArgs &a = b.m;
   const int lane = threadIdx.x & 31;
   const bool valid = L.r >= 0;
 
   // per-ray adjoint constants
-  int i_last = -1, i_clamp = -1;
+  int i_last = -1, i_clamp = -1, rank_clamp = -1;
   float ga_pre = 0.0f, gcr = 0.0f, gcg = 0.0f, gcb = 0.0f;
   float ga_s = 0.0f, gsr = 0.0f, gsg = 0.0f, gsb = 0.0f;
   if (valid) {
@@ -34,6 +35,7 @@ __device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs
     const float4 g = reinterpret_cast<const float4 *>(b.grad)[L.r];
     i_last = S.i_last;
     i_clamp = S.i_clamp;
+    if (SEQ) rank_clamp = S.rank_clamp;
     gcr = g.x;
     gcg = g.y;
     gcb = g.z;
@@ -80,6 +82,7 @@ __device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs
       const uint32_t rg = sh.erng[e][lane];
       const int lo = (int)(rg & 0xffffu), hi = (int)(rg >> 16);
       const float4 tk = __ldg(reinterpret_cast<const float4 *>(a.pose + k) + 2);  // {R22, t0, t1, t2}
+      const int rk = SEQ ? __ldg(a.rank + k) : 0;  // this primitive's leaf rank
       float2 acc[6];  // the 12 pose accumulators as packed pairs
 #pragma unroll
       for (int c = 0; c < 6; ++c) acc[c] = make_float2(0.0f, 0.0f);
@@ -95,6 +98,11 @@ __device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs
         const int i = lo + it;
         const bool in = it < cnt;
         if (!in) continue;
+        // sequential rule at the clamped sample: the primitive before the clamped one in
+        // BVH order is differentiated like a sample before it (role 1), the clamped one
+        // contributes w_J c_J (role 2), those after it nothing (role 3)
+        const int role = (i == i_clamp && rank_clamp >= 0) ? (rk < rank_clamp ? 1 : (rk == rank_clamp ? 2 : 3)) : 0;
+        if (role == 3) continue;
         float fx = 0.0f, fy = 0.0f, fz = 0.0f;
         float4 gv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         int vo = -1;
@@ -133,12 +141,13 @@ __device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs
           const float4 c10 = lerp4x2(c100, c101, wx, nwx), c11 = lerp4x2(c110, c111, wx, nwx);
           const float4 c0 = lerp4x2(c00, c01, wy, nwy), c1 = lerp4x2(c10, c11, wy, nwy);
           const float4 val = lerp4x2(c0, c1, splat2(fz), splat2(-fz));
-          const bool at_clamp = i == i_clamp;
+          const bool at_clamp = i == i_clamp && role == 0;
           const float ga = at_clamp ? ga_s : ga_pre;
           const float gr = at_clamp ? gsr : gcr, gg = at_clamp ? gsg : gcg, gb = at_clamp ? gsb : gcb;
           // dL/d(rgba) of this primitive's sample
-          gv = make_float4(a.dt * val.w * gr, a.dt * val.w * gg, a.dt * val.w * gb,
-                           a.dt * (ga + gr * val.x + gg * val.y + gb * val.z));
+          gv = role == 2 ? make_float4(gsr, gsg, gsb, 0.0f)  // w_J dL/dI
+                         : make_float4(a.dt * val.w * gr, a.dt * val.w * gg, a.dt * val.w * gb,
+                                       a.dt * (ga + gr * val.x + gg * val.y + gb * val.z));
           if (b.gmc) {
             // dval/du along each axis (zero along an axis where u was clamped), on packed pairs
             const float2 wz = splat2(fz), nwz = splat2(-fz);
@@ -210,7 +219,7 @@ __device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs
 
 // The tile schedule as in the frame kernel (its own cost record: the adjoint's
 // expensive tiles are not quite the forward's).
-template <int DT, int CAP, int MT>
+template <int DT, int CAP, int MT, bool SEQ>
 __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const MarchArgs &a = b.m;
@@ -227,7 +236,7 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
   load_lane_ray(L, a.o, a.d, tile_ray(a.geom, wt, lane));
   if (__ballot_sync(FULL, L.r >= 0) == 0) return;
   if (lane == 0) sh.clk = (unsigned int)clock();
-  backward_tile<DT, CAP, MT>(sh, b, L);
+  backward_tile<DT, CAP, MT, SEQ>(sh, b, L);
   if (a.cost) {
     __syncwarp();
     if (lane == 0) {
@@ -290,23 +299,25 @@ __global__ void k_pose_grads(const float *__restrict__ gmc, const Xform *__restr
   g_q[4 * k + 3] += (gz - z * dot) / nrm;
 }
 
-template <int DT, int CAP, int MT>
+template <int DT, int CAP, int MT, bool SEQ = false>
 static cudaError_t launch_bwd_t(const BwdArgs &b, cudaStream_t st) {
   size_t smem = sizeof(TileShared<CAP>) * TILE_WARPS;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_backward<DT, CAP, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_backward<DT, CAP, MT, SEQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   int64_t blocks = (b.m.geom.n_warp_tiles + TILE_WARPS - 1) / TILE_WARPS;
-  if (blocks > 0) k_backward<DT, CAP, MT><<<(unsigned)blocks, TILE_WARPS * 32, smem, st>>>(b);
+  if (blocks > 0) k_backward<DT, CAP, MT, SEQ><<<(unsigned)blocks, TILE_WARPS * 32, smem, st>>>(b);
   return cudaGetLastError();
 }
 
 template <int DT>
 static cudaError_t launch_bwd_m(const BwdArgs &b, cudaStream_t st) {
+  // the sequential rule's adjoint: one generic-M kernel per payload type
+  if (b.m.sequential) return launch_bwd_t<DT, MARCH_CAP, 0, true>(b, st);
   switch (b.m.M) {
     case 8: return launch_bwd_t<DT, MARCH_CAP, 8>(b, st);
     case 16: return launch_bwd_t<DT, MARCH_CAP, 16>(b, st);

@@ -59,12 +59,17 @@ struct __align__(16) Node {
   int right;
 };
 
-// Per-ray state saved by the forward for the adjoint (24 bytes).
-struct __align__(8) Saved {
+// Per-ray state saved by the forward for the adjoint (32 bytes). Under the
+// sequential rule a clamped ray keeps, instead of c/a and (1 - T)/a, the colour and
+// the weight of the primitive whose weight was clamped and that primitive's leaf rank
+// (rank_clamp = 0x7fffffff: none was; -1: the summed rule applied).
+struct __align__(16) Saved {
   float rho_r, rho_g, rho_b;  // c/a at the clamped sample
   float beta;                 // (1 - T)/a at the clamped sample
   int i_last;                 // last processed sample (-1: none)
   int i_clamp;                // clamped sample or -1
+  int rank_clamp;             // see above
+  int pad;
 };
 
 // ---------------------------------------------------------------- spec math

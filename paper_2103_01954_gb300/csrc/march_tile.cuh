@@ -126,23 +126,49 @@ __device__ __forceinline__ void order_window(TileShared<CAP> &sh, int ne, const 
 // A lane's saturating sample ii (its summed opacity exceeds 1 - T) blended the
 // paper's way: the window's primitives that contain it, one by one in BVH order
 // (sh.cand, from order_window), each adding w = min(alpha dt, 1 - T) of its colour,
-// until T = 1. x is the sample's world position.
+// until T = 1. x is the sample's world position. The adjoint's state: the colour,
+// weight and leaf rank of the primitive whose weight reached what was left (w >= 1 -
+// T; if rounding leaves every weight below it, the last primitive that contributed).
 template <int DT, int MT, int CAP>
 __device__ __forceinline__ void blend_sequential(const TileShared<CAP> &sh, int ne, const MarchArgs &a,
                                                  const float x[3], int ii, int M, float Mm1, float &T, float &Ir,
-                                                 float &Ig, float &Ib) {
+                                                 float &Ig, float &Ib, Saved &S) {
   const int lane = threadIdx.x & 31;
   float rem = 1.0f - T;
+  S = {0.0f, 0.0f, 0.0f, 0.0f, ii, ii, 0x7fffffff, 0};
+  int last = -1;  // the last contributing entry while none has been clamped
+  float4 vlast = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  float wlast = 0.0f;
   for (int p = 0; p < ne && rem > 0.0f; ++p) {
     const int e = sh.cand[p];
     const uint32_t r = sh.erng[e][lane];
     if ((int)(r & 0xffffu) > ii || (int)(r >> 16) < ii) continue;
     const float4 v = sample_rgba<DT, MT>(sh.exf[e], sh.eptr[e], x, M, Mm1, a.status);
-    const float w = fminf(v.w * a.dt, rem);
+    float w = v.w * a.dt;
+    if (w >= rem) {  // this primitive's weight is clamped to what is left
+      w = rem;
+      S.rho_r = v.x;
+      S.rho_g = v.y;
+      S.rho_b = v.z;
+      S.beta = w;
+      S.rank_clamp = __ldg(a.rank + sh.ek[e]);
+      last = -2;
+    } else if (w > 0.0f) {
+      last = e;
+      vlast = v;
+      wlast = w;
+    }
     Ir = fmaf(v.x, w, Ir);
     Ig = fmaf(v.y, w, Ig);
     Ib = fmaf(v.z, w, Ib);
     rem -= w;
+  }
+  if (last >= 0) {
+    S.rho_r = vlast.x;
+    S.rho_g = vlast.y;
+    S.rho_b = vlast.z;
+    S.beta = wlast;
+    S.rank_clamp = __ldg(a.rank + sh.ek[last]);
   }
   T = 1.0f;
 }
@@ -181,7 +207,7 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
       if (T >= a.stop_T) {
         alive = false;
         if (!COUNT && a.saved) {
-          Saved S = {0.0f, 0.0f, 0.0f, 0.0f, ii, -1};
+          Saved S = {0.0f, 0.0f, 0.0f, 0.0f, ii, -1, -1, 0};
           a.saved[L.r] = S;
         }
         saved_done = true;
@@ -194,7 +220,7 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
       T = 1.0f;
       alive = false;  // T = 1 >= 1 - eps_early
       if (!COUNT && a.saved) {
-        Saved S = {cr / aa, cg / aa, cb / aa, bt, ii, ii};
+        Saved S = {cr / aa, cg / aa, cb / aa, bt, ii, ii, -1, 0};
         a.saved[L.r] = S;
       }
       saved_done = true;
@@ -332,11 +358,9 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
       if (SEQ && seq_ii >= 0) {  // blend the saturating sample in BVH order
         const float ti = sample_t(a.t_near, a.dt, seq_ii);
         const float xq[3] = {fmaf(ti, L.d[0], L.o[0]), fmaf(ti, L.d[1], L.o[1]), fmaf(ti, L.d[2], L.o[2])};
-        blend_sequential<DT, MT, CAP>(sh, ne, a, xq, seq_ii, M, Mm1, T, Ir, Ig, Ib);
-        if (a.saved) {
-          Saved S = {0.0f, 0.0f, 0.0f, 0.0f, seq_ii, -1};
-          a.saved[L.r] = S;
-        }
+        Saved S;
+        blend_sequential<DT, MT, CAP>(sh, ne, a, xq, seq_ii, M, Mm1, T, Ir, Ig, Ib, S);
+        if (a.saved) a.saved[L.r] = S;
         saved_done = true;
       }
       i = ie;
@@ -359,7 +383,7 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
   float4 out = make_float4(fmaf(bgw, a.bg[0], Ir), fmaf(bgw, a.bg[1], Ig), fmaf(bgw, a.bg[2], Ib), T);
   reinterpret_cast<float4 *>(a.out)[L.r] = out;
   if (a.saved && !saved_done) {
-    Saved S = {0.0f, 0.0f, 0.0f, 0.0f, a.n_steps - 1, -1};
+    Saved S = {0.0f, 0.0f, 0.0f, 0.0f, a.n_steps - 1, -1, -1, 0};
     a.saved[L.r] = S;
   }
 }

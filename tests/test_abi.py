@@ -45,7 +45,7 @@ def test_host_only_calls():
     assert L.mvp_num_steps(1.0, 5.0, 0.01) == 400
     assert L.mvp_num_steps(1.0, 5.0, 0.005) == 800
     assert L.mvp_num_steps(1.0, 1.0, 0.01) == 0
-    assert L.mvp_saved_bytes(10) == 240
+    assert L.mvp_saved_bytes(10) == 320
     assert L.mvp_saved_bytes(0) == 0
 
 

@@ -100,7 +100,54 @@ def test_sequential_brute_equals_pruned(orc):
     np.testing.assert_allclose(a, b, atol=1e-12)
 
 
-def test_adjoint_rejects_sequential(orc):
-    sc, rays, _ = synthetic.make_config("tiny_8x8^3_64x64", 0)
-    with pytest.raises(ValueError):
-        orc.backward(sc, rays, np.zeros((rays.n, 4)), PRUNED32 | SEQ)
+def test_sequential_adjoint_closed_form(orc):
+    """The two-box scene, loss g . I: box A (lower x, first in BVH order) enters the
+    saturating sample whole, box B is clamped to what is left. Summed over each box's
+    voxels (a constant field: the trilinear weights of a sample sum to 1):
+    dL/dalpha_A = 3 dt g.(c_A - c_B), dL/dalpha_B = 0, dL/dc_A = 3 dt alpha_A g,
+    dL/dc_B = (2 dt alpha_B + w_B) g with w_B = 1 - 2 dt (alpha_A + alpha_B) - dt alpha_A."""
+    dt, aA, aB = 0.01, 17.0, 19.0
+    cA, cB = np.array([0.9, 0.1, 0.2]), np.array([0.1, 0.7, 0.4])
+    rays = rays_from([0, 0, -3], [0, 0, 1], 0.0037, 6.0, dt)
+    sc = _pair(0.05, -0.05, aB, aA, cB, cA)  # listed B first: the order must come from the positions
+    g = np.array([[0.3, -1.2, 0.7, 0.4]])
+    G = orc.backward(sc, rays, g, 3 | SEQ)["g_payload"]
+    cA32, cB32 = cA.astype(np.float32).astype(np.float64), cB.astype(np.float32).astype(np.float64)
+    wB = 1 - 2 * dt * (aA + aB) - dt * aA
+    gB, gA = G[0].reshape(-1, 4).sum(0), G[1].reshape(-1, 4).sum(0)  # scene order: B, A
+    np.testing.assert_allclose(gA[3], 3 * dt * g[0, :3] @ (cA32 - cB32), atol=1e-12)
+    assert abs(gB[3]) < 1e-12
+    np.testing.assert_allclose(gA[:3], 3 * dt * aA * g[0, :3], atol=1e-12)
+    np.testing.assert_allclose(gB[:3], (2 * dt * aB + wB) * g[0, :3], atol=1e-12)
+    # the summed rule on the same scene gives other values (it treats both boxes alike)
+    Gs = orc.backward(sc, rays, g, 3)["g_payload"]
+    assert abs(Gs[0].reshape(-1, 4).sum(0)[3]) > 1e-3
+
+
+def test_sequential_adjoint_matches_finite_differences(orc):
+    """Payload gradients of the sequential mode against central differences of its own
+    forward (the image is piecewise linear in the payload), on a scene where the rule
+    matters."""
+    from helpers import zero_boundary
+
+    sc, rays, _ = synthetic.make_config("diff_small_64x8^3_2x48x40", 1)
+    sc = zero_boundary(sc)
+    g = np.random.default_rng(6).standard_normal((rays.n, 4))
+    diff = np.abs(orc.render(sc, rays, 3 | SEQ)["rgba"] - orc.render(sc, rays, 3)["rgba"]).max()
+    assert diff > 1e-4  # the scene has saturating samples shared by several primitives
+    gp = orc.backward(sc, rays, g, 3 | SEQ)["g_payload"]
+    scale = np.abs(gp).max()
+
+    def loss(P):
+        return float((orc.render(synthetic.Scene(t=sc.t, q=sc.q, s=sc.s, payload=P, M=sc.M), rays,
+                                 3 | SEQ)["rgba"] * g).sum())
+
+    rng = np.random.default_rng(2)
+    nz = np.argwhere(np.abs(gp) > 1e-3 * scale)
+    for j in rng.choice(len(nz), 16, replace=False):
+        idx = tuple(nz[j])
+        a, b = sc.payload.copy(), sc.payload.copy()
+        a[idx] += 1e-3
+        b[idx] -= 1e-3
+        f = (loss(a) - loss(b)) / (float(a[idx]) - float(b[idx]))
+        assert abs(f - gp[idx]) <= 1e-6 * scale, (idx, f, gp[idx])
