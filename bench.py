@@ -341,8 +341,9 @@ def _cpu_baseline(seconds: float = 15.0):
     return {"value": total_rays / total_s / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
             "tiny_8x8^3_64x64_full_frame": {"seconds": round(tiny_s, 4),
                                             "mrays_per_s": round(r0.n / tiny_s / 1e6, 4)},
-            "sample": f"{total_rays} seeded random pixels of the 667x1024 frame (of 683008), FP64 oracle, "
-                      f"pruned mode, {cores} OpenMP threads, {total_s:.1f} s"}
+            "sample": f"{total_rays} rays in batches of seeded random pixels of the 667x1024 frame (683008 "
+                      f"pixels; batches drawn independently, so pixels may repeat), FP64 oracle, pruned mode, "
+                      f"{cores} OpenMP threads, {total_s:.1f} s"}
 
 
 def _ncu_record(kernel_key: str) -> dict:
