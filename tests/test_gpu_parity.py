@@ -420,3 +420,23 @@ def test_tile_schedule_changes_no_result():
         assert torch.equal(o, plain)
     ref = oracle.render(sc, rays, F32M)["rgba"]
     _check_image(plain.cpu().numpy(), ref, "tile schedule")
+
+
+def test_largest_sample_count_and_voxel_edge():
+    """The limits of the boundary: n_steps = MVP_MAX_STEPS (65535 samples, the largest
+    that the 16-bit sample ranges hold) and payload edge M = MVP_MAX_M (128)."""
+    sc = synthetic.make_scene(8, 8, 3, layout="sphere", s_const=0.3, empty_frac=0.5)
+    cam = synthetic.look_at_camera((0.0, 0.0, -3.0), 24, 20, 24.0)
+    rays = synthetic.make_rays([cam], 0.0, 6.55345, 1e-4)
+    assert rays.n_steps == 65535 == B.lib().mvp_num_steps(0.0, 6.55345, 1e-4)
+    out, _ = Dev(sc, rays).build().render()
+    ref = oracle.render(sc, rays, F32M)
+    _check_image(out.cpu().numpy(), ref["rgba"], "65535 samples")
+    assert ref["i_last"].max() == 65534 and (ref["rgba"][:, 3] > 0).mean() > 0.3
+    big = synthetic.make_scene(2, 128, 4, layout="sphere", s_const=0.6, empty_frac=0.3)
+    cam = synthetic.look_at_camera((0.2, 0.1, -3.0), 40, 32, 40.0)
+    rays = synthetic.make_rays([cam], 1.0, 5.0, 0.005)
+    out, _ = Dev(big, rays).build().render()
+    ref = oracle.render(big, rays, F32M)
+    _check_image(out.cpu().numpy(), ref["rgba"], "M = 128")
+    assert (ref["rgba"][:, 3] > 0).mean() > 0.3
