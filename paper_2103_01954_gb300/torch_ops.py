@@ -261,6 +261,27 @@ def camera_rays(ctx: Context, c2w, focal: float, width: int, height: int, out=No
     return o, d
 
 
+def allreduce_gradients(grads, group=None):
+    """The data-parallel backward's one exchange: ranks that marched disjoint sets of
+    rays (cameras, image rows) over the same primitives hold partial gradients whose
+    sum is the gradient of the whole batch (the loss is a sum over rays). Sums the
+    given tensors over the process group in place, as one flat collective (NCCL for
+    device tensors, gloo for host tensors). A no-op without an initialised group."""
+    import torch.distributed as dist
+
+    grads = [g for g in grads if g is not None]
+    if not grads or not dist.is_available() or not dist.is_initialized():
+        return grads
+    flat = torch.cat([g.reshape(-1) for g in grads])
+    dist.all_reduce(flat, op=dist.ReduceOp.SUM, group=group)
+    off = 0
+    for g in grads:
+        n = g.numel()
+        g.copy_(flat[off:off + n].view_as(g))
+        off += n
+    return grads
+
+
 class MVPRender(torch.autograd.Function):
     """Differentiable render: (t, q, s, payload) -> rgba [R, 4].
 
