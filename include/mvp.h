@@ -195,7 +195,8 @@ MVP_API size_t mvp_saved_bytes(int64_t n_rays);
  * only by the order of their float reductions). The first call at a new, larger
  * tile count allocates its buffers (cudaMalloc). Calls on other streams that overlap
  * the last scheduled one use the plain order. enable = 0 always uses the plain
- * order. */
+ * order; a frame (mvp_build_bvh at an unchanged or smaller primitive count, then
+ * mvp_raymarch_fwd) then only enqueues kernels and can be captured into a CUDA graph. */
 MVP_API mvp_status mvp_ctx_set_tile_schedule(mvp_ctx *ctx, int32_t enable);
 /* Render: out_rgba [n][4] float32 device = (I + (1 - A) bg, A). `saved`
  * (device, mvp_saved_bytes(n) bytes, nullable) receives the per-ray state the

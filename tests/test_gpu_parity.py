@@ -440,3 +440,30 @@ def test_largest_sample_count_and_voxel_edge():
     ref = oracle.render(big, rays, F32M)
     _check_image(out.cpu().numpy(), ref["rgba"], "M = 128")
     assert (ref["rgba"][:, 3] > 0).mean() > 0.3
+
+
+def test_frame_replays_as_a_cuda_graph():
+    """With the tile schedule off the frame (BVH rebuild + march) enqueues kernels only,
+    so it can be captured into a CUDA graph; replays give the eager image bit for bit."""
+    sc, rays, _ = synthetic.make_config("small_512x8^3_96x128", 2)
+    dv = Dev(sc, rays).build()
+    dv.ctx.set_tile_schedule(False)
+    eager, _ = dv.render()
+    out = torch.empty_like(eager)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):  # warm-up on the capture stream (no allocation inside the capture)
+        dv.bvh.build(dv.prims)
+        T.raymarch_fwd(dv.ctx, dv.prims, dv.bvh, dv.rs, out=out)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        dv.bvh.build(dv.prims)
+        T.raymarch_fwd(dv.ctx, dv.prims, dv.bvh, dv.rs, out=out)
+    for _ in range(3):
+        out.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, eager)
+    dv.ctx.sync()
