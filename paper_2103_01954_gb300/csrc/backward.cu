@@ -219,8 +219,12 @@ __device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs
 
 // The tile schedule as in the frame kernel (its own cost record: the adjoint's
 // expensive tiles are not quite the forward's).
+#ifndef MVP_BWD_MINB
+#define MVP_BWD_MINB 4  // resident blocks per SM the adjoint is compiled for
+#endif
+
 template <int DT, int CAP, int MT, bool SEQ>
-__global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_backward(BwdArgs b) {
+__global__ void __launch_bounds__(TILE_WARPS * 32, MVP_BWD_MINB) k_backward(BwdArgs b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const MarchArgs &a = b.m;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
