@@ -752,6 +752,7 @@ def run_gpu(args):
                          "image": "667x1024", "dt": 0.005, "t_range": [1.0, 5.0], "samples_per_ray": 800,
                          "saturated_ray_fraction": round(saturated, 4),
                          "step": "BVH rebuild + traversal + march", "l2": "flushed (512 MiB write) before each step",
+                         "stages_ms": {"bvh": round(ms - march_ms, 4), "march": round(march_ms, 4)},
                          "parallelism": f"replicas x{ws} (each rank its own frame)"},
               "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps}
     if ws > 1:
