@@ -70,8 +70,13 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 // resolution class (MT = M for M = 8, 16, 32, else 0: any M). The warp that counts
 // the last tile publishes the completion and resets the slot's counter for its next
 // request (every other warp of this request has counted by then).
+#ifndef MVP_SERVE_HALF_MINB
+#define MVP_SERVE_HALF_MINB 4  // resident blocks per SM of the BF16/FP16 serving kernels
+#endif
+
 template <int DT, int MT>
-__global__ void __launch_bounds__(TILE_WARPS * 32, MVP_MARCH_MINB) k_serve(const __grid_constant__ ServeReq R) {
+__global__ void __launch_bounds__(TILE_WARPS * 32, DT == MVP_F32 ? MVP_MARCH_MINB : MVP_SERVE_HALF_MINB)
+    k_serve(const __grid_constant__ ServeReq R) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   TileShared<SERVE_CAP> &sh = reinterpret_cast<TileShared<SERVE_CAP> *>(smem_raw)[warp];
