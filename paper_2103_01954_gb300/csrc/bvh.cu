@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(256) k_prims_partial(const float *__restrict__
                                                        float4 *__restrict__ pbox, float *__restrict__ partial,
                                                        int *status) {
   __shared__ float sb[8][6];
+  pdl_trigger();  // the one-block sort may be scheduled now; it waits for this grid
   const int k = blockIdx.x * 256 + threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
   if (k < n) {
@@ -319,6 +320,8 @@ __global__ void __launch_bounds__(SORT1_THREADS) k_sort_one(const float *__restr
   __shared__ int base[SORT1_BINS + 1];
   __shared__ int tile_total[SORT1_BINS];
   __shared__ float sscene[6];
+  pdl_wait();
+  pdl_trigger();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
   // centre bounds from the partials, then the codes (into kb/vb: the odd pass count
@@ -565,6 +568,8 @@ __global__ void __launch_bounds__(HIER_THREADS) k_hierarchy(const uint32_t *__re
                                                             int2 *__restrict__ range, float4 *__restrict__ chunk1,
                                                             float4 *__restrict__ chunk2, int *__restrict__ rank) {
   __shared__ float sc[32][6];
+  pdl_wait();
+  pdl_trigger();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i = blockIdx.x * HIER_THREADS + tid;
   float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
@@ -620,6 +625,8 @@ __global__ void __launch_bounds__(REFIT_WARPS * 32) k_refit_ranges(Node *__restr
                                                                    const int2 *__restrict__ range,
                                                                    const float4 *__restrict__ chunk1,
                                                                    const float4 *__restrict__ chunk2, int n) {
+  pdl_wait();
+  pdl_trigger();  // the march may be scheduled now; it waits for this grid
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * REFIT_WARPS + (threadIdx.x >> 5);
   if (i >= n - 1) return;
@@ -740,8 +747,11 @@ cudaError_t bvh_build(BvhBuffers &b, const float *t, const float *q, const float
     }
     float *partial = reinterpret_cast<float *>(b.counts);  // 6 floats per 256 primitives
     k_prims_partial<<<n_partial, 256, 0, st>>>(t, q, s, n, M, b.pose, b.xf, b.pbox, partial, status);
-    k_sort_one<<<1, SORT1_THREADS, SORT1_SMEM, st>>>(t, n, partial, n_partial, b.scene, b.keys_a, b.vals_a,
-                                                     b.keys_b, b.vals_b);
+    // the rest of the chain is scheduled while its predecessor finishes (each kernel
+    // waits for it before touching memory)
+    cudaError_t e = pdl_launch(k_sort_one, dim3(1), dim3(SORT1_THREADS), SORT1_SMEM, st, t, n,
+                               (const float *)partial, n_partial, b.scene, b.keys_a, b.vals_a, b.keys_b, b.vals_b);
+    if (e != cudaSuccess) return e;
   } else {
     k_bounds<<<1, 1024, 0, st>>>(t, n, b.scene);
     k_prims<<<(n + 255) / 256, 256, 0, st>>>(t, q, s, n, M, b.scene, b.pose, b.xf, b.pbox, b.keys_a, b.vals_a,
@@ -762,12 +772,13 @@ cudaError_t bvh_build(BvhBuffers &b, const float *t, const float *q, const float
   // second key and value buffers (n/32 and n/1024 boxes of 32 bytes fit in 4n bytes)
   int2 *range = reinterpret_cast<int2 *>(b.parent);
   float4 *chunk1 = reinterpret_cast<float4 *>(b.keys_b), *chunk2 = reinterpret_cast<float4 *>(b.vals_b);
-  k_hierarchy<<<(n + HIER_THREADS - 1) / HIER_THREADS, HIER_THREADS, 0, st>>>(b.keys_a, b.vals_a, n, b.pbox, b.nodes,
-                                                                              range, chunk1, chunk2, b.rank);
-  if (n > 1)
-    k_refit_ranges<<<(n - 1 + REFIT_WARPS - 1) / REFIT_WARPS, REFIT_WARPS * 32, 0, st>>>(b.nodes, range, chunk1,
-                                                                                          chunk2, n);
-  return cudaGetLastError();
+  cudaError_t e = pdl_launch(k_hierarchy, dim3((n + HIER_THREADS - 1) / HIER_THREADS), dim3(HIER_THREADS), 0, st,
+                             (const uint32_t *)b.keys_a, (const int *)b.vals_a, n, (const float4 *)b.pbox, b.nodes,
+                             range, chunk1, chunk2, b.rank);
+  if (e == cudaSuccess && n > 1)
+    e = pdl_launch(k_refit_ranges, dim3((n - 1 + REFIT_WARPS - 1) / REFIT_WARPS), dim3(REFIT_WARPS * 32), 0, st,
+                   b.nodes, (const int2 *)range, (const float4 *)chunk1, (const float4 *)chunk2, n);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 __global__ void k_export_keys(const uint32_t *__restrict__ km, const int *__restrict__ kv, int n,

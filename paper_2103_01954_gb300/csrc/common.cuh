@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/mvp.h"
 
 namespace mvp {
@@ -23,6 +25,30 @@ constexpr int STATUS_CAPACITY = 1;
 constexpr int STATUS_DEVICE = 2;
 constexpr int STATUS_POSE = 4;  // a primitive's t, q or s is not finite, |q| = 0 or s <= 0
 constexpr int STATUS_BOUNDS = 8;  // checked builds: an index fell outside its array (access skipped)
+
+// Programmatic dependent launch: a kernel started with pdl_launch may be scheduled
+// while the kernel before it in the stream is still running; it calls pdl_wait()
+// before its first global-memory access (afterwards everything earlier work wrote is
+// visible), so only its launch overlaps. pdl_trigger() lets the next such kernel be
+// scheduled early. Both are no-ops for kernels launched the ordinary way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Checked builds (-DMVP_CHECK_BOUNDS, the stand-in for a memory checker): an index
 // outside its array sets STATUS_BOUNDS and the access is skipped. Elsewhere the

@@ -9,6 +9,7 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, MVP_MARCH_MINB) k_march(March
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   TileShared<CAP> &sh = reinterpret_cast<TileShared<CAP> *>(smem_raw)[warp];
+  pdl_wait();  // whatever ran before (the BVH refit, usually) is complete and visible
   const int64_t slot = (int64_t)blockIdx.x * TILE_WARPS + warp;
   if (slot >= a.geom.n_warp_tiles) return;
   int64_t wt = slot;
@@ -156,8 +157,7 @@ static cudaError_t launch_march_t(const MarchArgs &a, cudaStream_t st) {
   }
   int64_t blocks = (a.geom.n_warp_tiles + TILE_WARPS - 1) / TILE_WARPS;
   if (blocks == 0) return cudaSuccess;
-  k_march<DT, CAP, COUNT, MT, SEQ><<<(unsigned)blocks, TILE_WARPS * 32, smem, st>>>(a);
-  return cudaGetLastError();
+  return pdl_launch(k_march<DT, CAP, COUNT, MT, SEQ>, dim3((unsigned)blocks), dim3(TILE_WARPS * 32), smem, st, a);
 }
 
 template <int DT, bool COUNT>
