@@ -311,6 +311,14 @@ def _e2e(torch, T, info, steps, warmup, payload_dtype="f32", rays_from="camera")
             else "copied from the host every frame"}
 
 
+def _host_threads() -> int:
+    """Host cores this process may run on; the oracle is given exactly this many threads."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
 def _cpu_baseline(seconds: float = 15.0):
     """The oracle (FP64, pruned mode, FP32 membership) on a seeded ray sample of the
     workload, on all host cores."""
@@ -321,22 +329,22 @@ def _cpu_baseline(seconds: float = 15.0):
     scene, rays, _ = synthetic.make_config(WORKLOAD, 0)
     rng = np.random.default_rng(123)
     n = 256
+    cores = _host_threads()
     total_rays, total_s = 0, 0.0
     while total_s < seconds:
         sel = rng.choice(rays.n, n, replace=False)
         sub = synthetic.Rays(o=rays.o[sel], d=rays.d[sel], t_near=rays.t_near, t_far=rays.t_far, dt=rays.dt)
         t0 = time.perf_counter()
-        oracle.render(scene, sub)
+        oracle.render(scene, sub, n_threads=cores)
         dt = time.perf_counter() - t0
         total_rays += n
         total_s += dt
         if dt < seconds / 8:
             n *= 2
-    cores = os.cpu_count()
     # the whole tiny frame (8 primitives of 8^3, 64x64), as a second reference point
     s0, r0, _ = synthetic.make_config("tiny_8x8^3_64x64", 0)
     t0 = time.perf_counter()
-    oracle.render(s0, r0)
+    oracle.render(s0, r0, n_threads=cores)
     tiny_s = time.perf_counter() - t0
     return {"value": total_rays / total_s / 1e6, "unit": "Mrays/s", "cores": cores, "kind": "oracle",
             "tiny_8x8^3_64x64_full_frame": {"seconds": round(tiny_s, 4),
@@ -837,11 +845,12 @@ def run_reference(args):
     scene, rays, _ = synthetic.make_config(WORKLOAD, 0)
     rng = np.random.default_rng(7)
     n = 2048
+    cores = _host_threads()
 
     def step():
         sel = rng.choice(rays.n, n, replace=False)
         sub = synthetic.Rays(o=rays.o[sel], d=rays.d[sel], t_near=rays.t_near, t_far=rays.t_far, dt=rays.dt)
-        oracle.render(scene, sub)
+        oracle.render(scene, sub, n_threads=cores)
 
     for _ in range(args.warmup):
         step()
@@ -850,7 +859,6 @@ def run_reference(args):
         step()
     sec = (time.perf_counter() - t0) / args.steps
     v = n / sec / 1e6
-    cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "Mrays/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
