@@ -69,11 +69,26 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples during the timed region."""
+    """nvidia-smi clock / throttle samples during the timed region.
 
-    def __init__(self, index: int):
+    Each sample carries nvidia-smi's own timestamp; the summary keeps those taken between
+    the region's start and end (host wall clock), so it does not depend on when the
+    samples reach the file. The region starts once nvidia-smi has written its first
+    sample (bounded wait), so its start-up does not eat the region. A region shorter
+    than the sampling interval holds no sample; then the last sample before it and the
+    first after it stand in, labelled as such."""
+
+    QUERY = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+    REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, index: int, interval_ms: int = 50, start_timeout_s: float = 5.0):
         self.index = index
+        self.interval_ms = interval_ms
+        self.start_timeout_s = start_timeout_s
         self.proc = None
+        self.t0 = self.t1 = 0.0  # the region, host wall clock (s)
         # the raw samples go to $MVP_BENCH_OUT (default: the system's temporary directory)
         out_dir = os.environ.get("MVP_BENCH_OUT") or tempfile.gettempdir()
         self.path = os.path.join(out_dir, f"clocks_{os.getpid()}.csv")
@@ -83,17 +98,21 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.index}",
-                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
-                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", str(self.interval_ms)],
                 stdout=self.f, stderr=subprocess.DEVNULL)
+            t_end = time.monotonic() + self.start_timeout_s
+            while os.path.getsize(self.path) == 0 and time.monotonic() < t_end and self.proc.poll() is None:
+                time.sleep(0.005)
         except Exception:
             self.proc = None
+        self.t0 = time.time()
         return self
 
     def __exit__(self, *a):
+        self.t1 = time.time()
         if self.proc is not None:
+            time.sleep(3 * self.interval_ms / 1e3)  # a sample after the region
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -101,25 +120,37 @@ class ClockSampler:
                 self.proc.kill()
             self.f.close()
 
+    @staticmethod
+    def _when(stamp: str):
+        import datetime
+
+        try:
+            return datetime.datetime.strptime(stamp.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         rows = []
         for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 7:
-                try:
-                    rows.append(parts)
-                except Exception:
-                    pass
-        if not rows:
+            r = [x.strip() for x in line.split(",")]
+            if len(r) >= 8 and self._when(r[0]) is not None:
+                rows.append((self._when(r[0]), r[1:]))
+        window = "timed region"
+        sel = [r for ts, r in rows if self.t0 <= ts <= self.t1]
+        if not sel:
+            before = [r for ts, r in rows if ts < self.t0][-1:]
+            after = [r for ts, r in rows if ts > self.t1][:1]
+            sel = before + after
+            window = "bracketing the timed region (shorter than the sampling interval)"
+        if not sel:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower() == "active"})
+        sm = [float(r[0]) for r in sel if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in sel if r[1].replace(".", "").isdigit()]
+        reasons = sorted({self.REASONS[i] for r in sel for i in range(4) if r[3 + i].lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(sel), "window": window, "interval_ms": self.interval_ms}
 
 
 def _frame_runner(cfg: str, seed: int, dtype: str, want_bwd: bool, torch, T, synthetic, sequential=False,
@@ -890,7 +921,7 @@ def run_profile(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--quick", action="store_true", help="headline figure only")
