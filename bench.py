@@ -578,6 +578,36 @@ def _fade_pack(torch, T, synthetic, peaks):
             "bytes_per_voxel": 24, "voxels": n_vox, "workload": WORKLOAD}
 
 
+def _pack(torch, T, synthetic, peaks):
+    """The FP32 -> BF16 / FP16 payload conversion (mvp_pack_payload) on the paper-scale
+    payload (4096 x 16^3 voxels): 16 bytes read and 8 written per voxel, against the
+    measured HBM copy bandwidth."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sc, _, _ = synthetic.make_config(WORKLOAD, 0)
+    ctx = T.Context(dev.index)
+    p32 = torch.from_numpy(sc.payload).to(dev)
+    n_vox = p32.numel() // 4
+    res = {"bytes_per_voxel": 24, "voxels": n_vox, "workload": WORKLOAD}
+    for name, tdt in (("bf16", torch.bfloat16), ("f16", torch.float16)):
+        for _ in range(3):
+            out = T.pack_payload(ctx, p32, tdt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = 20
+        e0.record()
+        for _ in range(n):
+            out = T.pack_payload(ctx, p32, tdt)
+        e1.record()
+        torch.cuda.synchronize()
+        ctx.sync()
+        ms = e0.elapsed_time(e1) / n
+        gbps = 24.0 * n_vox / (ms * 1e-3) / 1e9
+        res[name] = {"ms": round(ms, 4), "GBps": round(gbps, 1),
+                     "hbm_frac": round(gbps / peaks["hbm_gbs"], 3) if peaks.get("hbm_gbs") else None}
+        del out
+    return res
+
+
 def _serve_trace(T, srv, ids, reqs, arrivals):
     """Submit `reqs` at their Poisson arrival times and poll until all are done.
     Returns (latencies in ms, wall seconds)."""
@@ -841,6 +871,7 @@ def run_gpu(args):
         del st, inf
         torch.cuda.empty_cache()
         variants["fade_pack_bf16"] = _fade_pack(torch, T, synthetic, peaks)
+        variants["pack"] = _pack(torch, T, synthetic, peaks)
         variants["vr_stereo_896x832"] = _vr_stereo(torch, T, synthetic, flush)
         variants["vr_stereo_view_dependent_896x832"] = _vr_stereo(torch, T, synthetic, flush, view_dependent=True)
         if variants.get("fwd_bf16"):
