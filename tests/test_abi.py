@@ -1,9 +1,11 @@
 """The C ABI library builds, loads and exports every function include/mvp.h
-declares; host-only calls (no GPU needed) behave as documented."""
+declares; host-only calls (no GPU needed) behave as documented; without the library
+the Python entry points raise instead of falling back."""
 import ctypes
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -74,3 +76,34 @@ def test_invalid_arguments_rejected_on_host():
     pr = B.mvp_prims(n=1, M=1, dtype=0)
     assert L.mvp_build_bvh(None, ctypes.byref(pr), None, None) == B.MVP_ERR_INVALID_ARG
     assert L.mvp_raymarch_fwd(None, ctypes.byref(pr), None, None, None, None, None) == B.MVP_ERR_INVALID_ARG
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """With no built library and no compiler, the binding and the torch entry points raise;
+    nothing falls back to another implementation."""
+    script = f"""
+import sys
+sys.path.insert(0, {ROOT!r})
+import paper_2103_01954_gb300.build as Bd
+Bd.BUILD = {str(tmp_path)!r}
+def _no_nvcc():
+    raise RuntimeError("nvcc not found")
+Bd._nvcc = _no_nvcc
+from paper_2103_01954_gb300 import binding as B
+try:
+    B.lib()
+    print("LOADED")
+except RuntimeError as e:
+    print("RAISED", e)
+from paper_2103_01954_gb300 import torch_ops as T
+try:
+    T.Context(0)
+    print("CONTEXT")
+except Exception as e:
+    print("RAISED", type(e).__name__)
+"""
+    out = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True, timeout=300)
+    lines = out.stdout.strip().splitlines()
+    assert len(lines) == 2, (out.stdout, out.stderr[-2000:])
+    assert lines[0].startswith("RAISED") and "nvcc not found" in lines[0]
+    assert lines[1].startswith("RAISED")
