@@ -822,6 +822,8 @@ def run_gpu(args):
                          "saturated_ray_fraction": round(saturated, 4),
                          "step": "BVH rebuild + traversal + march", "l2": "flushed (512 MiB write) before each step",
                          "stages_ms": {"bvh": round(ms - march_ms, 4), "march": round(march_ms, 4)},
+                         "ms_per_step_median": round(float(np.median(durs)), 4),
+                         "ms_per_step_p99": round(float(np.percentile(durs, 99)), 4),
                          "parallelism": f"replicas x{ws} (each rank its own frame)"},
               "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps}
     if ws > 1:
