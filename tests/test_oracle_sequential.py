@@ -151,3 +151,20 @@ def test_sequential_adjoint_matches_finite_differences(orc):
         b[idx] -= 1e-3
         f = (loss(a) - loss(b)) / (float(a[idx]) - float(b[idx]))
         assert abs(f - gp[idx]) <= 1e-6 * scale, (idx, f, gp[idx])
+
+
+def test_sequential_composes_with_the_literal_background(orc):
+    """The two ray flags act on different steps: the sequential rule changes the
+    saturating sample's blend, the literal reading only the background composite
+    (Sec. 3.1.4). Together, the image is the literal composite of the sequential result."""
+    sc, rays, _ = synthetic.make_config("tiny_8x8^3_64x64", 2)
+    bg = (0.25, 0.5, 1.0)
+    rays.bg = bg
+    seq = orc.render(sc, rays, PRUNED32 | SEQ)["rgba"]
+    both = orc.render(sc, rays, PRUNED32 | SEQ | 8)["rgba"]
+    B = np.float32(bg).astype(np.float64)[None]
+    A = seq[:, 3:4]
+    np.testing.assert_array_equal(both[:, 3], seq[:, 3])
+    np.testing.assert_allclose(both[:, :3], A * (seq[:, :3] - (1 - A) * B) + (1 - A) * B, atol=1e-12)
+    summed_literal = orc.render(sc, rays, PRUNED32 | 8)["rgba"]
+    assert np.abs(both - summed_literal).max() > 1e-4
