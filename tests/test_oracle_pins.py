@@ -455,3 +455,34 @@ def test_inputs_deterministic_and_shaped():
     np.testing.assert_allclose(np.linalg.norm(rays.d, axis=1), 1.0, atol=1e-6)
     assert abs((sc.payload[..., 3] == 0).mean() - 0.5) < 0.03
     assert np.allclose(np.linalg.norm(sc.t, axis=1), 1.0, atol=1e-6)
+
+
+def test_paper_scale_inputs_follow_the_recipe():
+    """The benchmark frame's inputs: 4096 primitives of 16^3 on an ellipsoid shell of radii
+    (1, 1.2, 0.9) with N(0, 0.02^2) jitter, half extents U[0.04, 0.08], 60 % empty voxels,
+    alpha = 4 softplus(N(0, 1)), one 667x1024 camera at radius 3 looking at the centre,
+    dt = 0.005 over [1, 5] (800 samples); the differentiation workload adds the opacity
+    fade window and four 512x512 cameras with a seeded target."""
+    sc, rays, _ = synthetic.make_config("paper_4096x16^3_667x1024", 0)
+    assert sc.payload.shape == (4096, 16, 16, 16, 4) and sc.payload.dtype == np.float32
+    assert rays.o.shape == (683008, 3) and (rays.width, rays.height) == (667, 1024)
+    assert rays.n_steps == 800 and (rays.t_near, rays.t_far, rays.dt) == (1.0, 5.0, 0.005)
+    assert sc.s.min() >= 0.04 and sc.s.max() <= 0.08
+    np.testing.assert_allclose(np.linalg.norm(sc.q, axis=1), 1.0, atol=1e-6)
+    radial = np.linalg.norm(sc.t / np.float32([1.0, 1.2, 0.9]), axis=1)
+    assert abs(np.median(radial) - 1.0) < 0.01 and radial.min() > 0.85 and radial.max() < 1.15
+    a = sc.payload[..., 3]
+    empty = (sc.payload == 0).all(-1)
+    assert abs(empty.mean() - 0.6) < 0.005
+    # mean of 4 softplus(z) over the occupied voxels: 4 E[softplus(N(0,1))] = 3.226
+    assert abs(a[~empty].mean() - 3.226) < 0.01
+    np.testing.assert_allclose(np.linalg.norm(rays.o[0]), 3.0, rtol=1e-6)
+    centre = rays.d[(1024 // 2) * 667 + 667 // 2]
+    np.testing.assert_allclose(centre, -rays.o[0] / 3.0, atol=2e-3)
+    sc3, rays3, extra = synthetic.make_config("diff_512x32^3_4x512x512", 0)
+    assert sc3.payload.shape == (512, 32, 32, 32, 4) and rays3.n == 4 * 512 * 512
+    assert extra["target"].shape == (rays3.n, 3)
+    # the fade window leaves the centre voxel's opacity (nearly) whole and zeroes the corners
+    occupied = sc3.payload[..., 3] > 0
+    assert sc3.payload[:, 0, 0, 0, 3].max() < 1e-6 * sc3.payload[..., 3].max()
+    assert occupied[:, 15:17, 15:17, 15:17].mean() > 0.3
