@@ -107,3 +107,29 @@ except Exception as e:
     assert len(lines) == 2, (out.stdout, out.stderr[-2000:])
     assert lines[0].startswith("RAISED") and "nvcc not found" in lines[0]
     assert lines[1].startswith("RAISED")
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the header's size and field offsets (a C
+    program compiled against include/mvp.h prints them)."""
+    structs = [B.mvp_prims, B.mvp_rays, B.mvp_request, B.mvp_serve_info]
+    lines = ['#include <stdio.h>', '#include "mvp.h"', "int main(void) {"]
+    for S in structs:
+        n = S.__name__
+        lines.append(f'  printf("{n} size %zu\\n", sizeof({n}));')
+        for f, _ in S._fields_:
+            lines.append(f'  printf("{n} {f} %zu\\n", offsetof({n}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        a, b, v = ln.split()
+        got[(a, b)] = int(v)
+    for S in structs:
+        n = S.__name__
+        assert got[(n, "size")] == ctypes.sizeof(S), n
+        for f, _ in S._fields_:
+            assert got[(n, f)] == getattr(S, f).offset, (n, f)
