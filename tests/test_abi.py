@@ -133,3 +133,34 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(n, "size")] == ctypes.sizeof(S), n
         for f, _ in S._fields_:
             assert got[(n, f)] == getattr(S, f).offset, (n, f)
+
+
+def test_binding_signatures_match_the_prototypes():
+    """Each function's ctypes signature has the prototype's argument count, a pointer
+    wherever the prototype takes one, and the same scalar type otherwise (a mismatch
+    would pass garbage through the ABI without an error)."""
+    hdr = open(os.path.join(ROOT, "include", "mvp.h")).read()
+    hdr = re.sub(r"\s+", " ", re.sub(r"/\*.*?\*/", "", hdr, flags=re.S))
+    protos = {m.group(2): (m.group(1), m.group(3).strip())
+              for m in re.finditer(r"([\w\s\*]*?)\b(mvp_\w+)\s*\(([^;{)]*)\)\s*;", hdr)}
+    scalar = {"int": ctypes.c_int32, "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64,
+              "uint64_t": ctypes.c_uint64, "size_t": ctypes.c_size_t, "float": ctypes.c_float,
+              "double": ctypes.c_double}
+    returns = {"const char *": ctypes.c_char_p, "mvp_status": ctypes.c_int32, "void": None,
+               "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "size_t": ctypes.c_size_t}
+
+    def is_pointer(t):
+        return t in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(t, ctypes._Pointer)
+
+    for name, res, args in B._SIGS:
+        ret, params = protos[name]
+        ret = ret.split("MVP_API")[-1].strip()
+        assert returns[ret] is res, (name, ret, res)
+        params = [] if params in ("", "void") else [p.strip() for p in params.split(",")]
+        assert len(params) == len(args), (name, params)
+        for p, a in zip(params, args):
+            ptype = " ".join(p.split()[:-1])
+            if "*" in p or ptype == "mvp_stream":
+                assert is_pointer(a), (name, p, a)
+            else:
+                assert scalar[ptype] is a, (name, p, a)
