@@ -164,3 +164,26 @@ def test_binding_signatures_match_the_prototypes():
                 assert is_pointer(a), (name, p, a)
             else:
                 assert scalar[ptype] is a, (name, p, a)
+
+
+def test_binding_constants_match_the_header():
+    """Status codes, payload types and ray flags: every name the binding defines has the
+    header's value (from the enums and #defines, read as text and evaluated by a C
+    program compiled against the header)."""
+    names = [n for n in dir(B) if n.startswith("MVP_") and isinstance(getattr(B, n), int)]
+    assert {"MVP_OK", "MVP_ERR_CAPACITY", "MVP_BF16", "MVP_BLEND_SEQUENTIAL"} <= set(names)
+    import tempfile
+
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "consts.c")
+        with open(src, "w") as f:
+            f.write('#include <stdio.h>\n#include "mvp.h"\nint main(void) {\n')
+            for n in names:
+                f.write(f'  printf("{n} %lld\\n", (long long)({n}));\n')
+            f.write("  return 0;\n}\n")
+        exe = os.path.join(d, "consts")
+        subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    got = {a: int(b) for a, b in (ln.split() for ln in out.splitlines())}
+    for n in names:
+        assert got[n] == getattr(B, n), n
