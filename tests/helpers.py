@@ -58,3 +58,18 @@ def zero_boundary(sc):
     p[:, :, :, 0] = 0
     p[:, :, :, -1] = 0
     return synthetic.Scene(t=sc.t, q=sc.q, s=sc.s, payload=p, M=sc.M)
+
+
+def rays_from_matrix(m34, focal, width, height, t_near, t_far, dt):
+    """Pinhole rays of a row-major 3x4 camera matrix [right down forward | eye] (the
+    matrix a serving request carries), through pixel centres (col + 0.5, row + 0.5)
+    about the image centre, computed in FP64 and stored FP32 (row-major pixels)."""
+    m = np.asarray(m34, np.float64).reshape(3, 4)
+    cols = (np.arange(width) + 0.5 - width / 2.0) / float(np.float32(focal))
+    rows = (np.arange(height) + 0.5 - height / 2.0) / float(np.float32(focal))
+    xx, yy = np.meshgrid(cols, rows)
+    dc = np.stack([xx, yy, np.ones_like(xx)], axis=-1).reshape(-1, 3)
+    d = dc @ m[:, :3].T
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    o = np.broadcast_to(m[:, 3], d.shape)
+    return rays_from(o, d, t_near, t_far, dt, width=width, height=height)

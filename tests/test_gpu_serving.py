@@ -2,14 +2,19 @@
 
 Each request's image must equal mvp_camera_rays + mvp_raymarch_fwd on the same
 avatar, and must be the same whether the request runs alone or in a mix of many
-concurrent requests of other avatars, cameras and resolutions. Admission honours
-the HBM budget; oversize requests are refused; waits time out on the host.
+concurrent requests of other avatars, cameras and resolutions. Every served image
+(alone, in the mix, each eye of a binocular request) also meets the FP64 oracle at
+the definition bar. Admission honours the HBM budget; oversize requests are refused;
+waits time out on the host.
 """
 import numpy as np
 import pytest
 import torch
 
+import oracle
 import synthetic
+from helpers import rays_from_matrix
+from parity_rules import definition_bar
 
 pytestmark = pytest.mark.gpu
 
@@ -21,14 +26,19 @@ from paper_2103_01954_gb300 import binding as B  # noqa: E402
 from paper_2103_01954_gb300 import torch_ops as T  # noqa: E402
 
 T_NEAR, T_FAR, DT = 1.0, 5.0, 0.01
+F64M = oracle.MODE_PRUNED | oracle.MEMBER_F64
+SPECS = [(256, 8, torch.float32, 0), (1024, 6, torch.bfloat16, 1), (64, 16, torch.float16, 2)]
+
+
+def _scene(n, M, seed):
+    return synthetic.make_scene(n, M, seed, layout="shell", s_range=(0.04 * (4096 / n) ** 0.5, 0.08 * (4096 / n) ** 0.5))
 
 
 def _avatars(ctx):
     """Three small avatars of different sizes and payload types (FP32, BF16, FP16)."""
-    specs = [(256, 8, torch.float32, 0), (1024, 6, torch.bfloat16, 1), (64, 16, torch.float16, 2)]
     out = []
-    for n, M, dt, seed in specs:
-        sc = synthetic.make_scene(n, M, seed, layout="shell", s_range=(0.04 * (4096 / n) ** 0.5, 0.08 * (4096 / n) ** 0.5))
+    for n, M, dt, seed in SPECS:
+        sc = _scene(n, M, seed)
         t = torch.from_numpy(sc.t).to(DEV)
         q = torch.from_numpy(sc.q).to(DEV)
         s = torch.from_numpy(sc.s).to(DEV)
@@ -36,6 +46,24 @@ def _avatars(ctx):
         p = p32 if dt == torch.float32 else T.pack_payload(ctx, p32, dt)
         out.append((t, q, s, p))
     return out
+
+
+def _oracle_scenes():
+    """The avatars as the oracle sees them: BF16 / FP16 payloads dequantised (the exact
+    values the kernel reads)."""
+    out = []
+    for n, M, dt, seed in SPECS:
+        sc = _scene(n, M, seed)
+        if dt != torch.float32:
+            sc = synthetic.Scene(t=sc.t, q=sc.q, s=sc.s, M=sc.M,
+                                 payload=torch.from_numpy(sc.payload).to(dt).float().numpy())
+        out.append(sc)
+    return out
+
+
+def _oracle_image(sc, cam, w, h):
+    rays = rays_from_matrix(cam, float(w), w, h, T_NEAR, T_FAR, DT)
+    return oracle.render(sc, rays, F64M)
 
 
 def _reference(ctx, av, cam, focal, w, h):
@@ -251,4 +279,55 @@ def test_cancel_queued_and_running_requests():
     assert st["cancelled"] == 2 and st["completed"] == 4
     assert st["pending"] == 0 and st["in_flight"] == 0 and st["in_flight_bytes"] == 0
     assert st["device_status"] == 0
+    srv.close()
+
+
+def test_served_images_match_the_oracle():
+    """Every served image against the FP64 oracle at the definition bar: requests of three
+    avatars (FP32, BF16, FP16 payloads) at several resolutions, rendered alone, then all
+    at once in a mix, and binocular requests (each eye). The oracle's rays come from the
+    request's own camera matrix through an FP64 pinhole model."""
+    torch.cuda.set_device(0)
+    ctx = T.Context(0)
+    avs = _avatars(ctx)
+    scenes = _oracle_scenes()
+    srv = T.Server(ctx, hbm_budget=2 << 30, max_slots=16)
+    ids = [srv.register(*a) for a in avs]
+    sizes = [(64, 48), (96, 96), (33, 70), (128, 64)]
+    cams = _cams(9, 31)
+    reqs = [(i % 3, cams[i], sizes[i % 4]) for i in range(9)]
+
+    def submit(k, cam, w, h, right=None):
+        return srv.submit_raw(T.Server.request(ids[k], cam, float(w), w, h, T_NEAR, T_FAR, DT, c2w_right=right))
+
+    alone = []
+    for k, cam, (w, h) in reqs:
+        out = torch.empty((h * w, 4), dtype=torch.float32, device=DEV)
+        st, _ = srv.wait(submit(k, cam, w, h), 10000.0, out)
+        assert st == B.MVP_OK
+        alone.append(out.cpu().numpy())
+    tks = [submit(k, cam, w, h) for k, cam, (w, h) in reqs]
+    mix = [torch.empty((h * w, 4), dtype=torch.float32, device=DEV) for _, _, (w, h) in reqs]
+    for j in reversed(range(len(tks))):
+        st, _ = srv.wait(tks[j], 10000.0, mix[j])
+        assert st == B.MVP_OK
+    assert srv.stats()["max_in_flight"] >= 4
+    for (k, cam, (w, h)), a, m in zip(reqs, alone, mix):
+        ref = _oracle_image(scenes[k], cam, w, h)
+        label = f"served avatar {k} {w}x{h}"
+        definition_bar(a, ref, label + " alone")
+        definition_bar(m.cpu().numpy(), ref, label + " in the mix")
+        assert (ref["rgba"][:, 3] > 0).mean() > 0.05
+    # binocular requests: each eye against the oracle's image of that eye's camera
+    w, h = 72, 56
+    for k in range(3):
+        cam = cams[k]
+        right = cam.copy()
+        right[:, 3] += np.float32(0.064) * right[:, 0]
+        both = torch.empty((2, h * w, 4), dtype=torch.float32, device=DEV)
+        st, _ = srv.wait(submit(k, cam, w, h, right), 10000.0, both)
+        assert st == B.MVP_OK
+        for eye, c in ((0, cam), (1, right)):
+            definition_bar(both[eye].cpu().numpy(), _oracle_image(scenes[k], c, w, h), f"stereo avatar {k} eye {eye}")
+    assert srv.stats()["device_status"] == 0
     srv.close()
