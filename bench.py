@@ -186,7 +186,7 @@ def _frame_runner(cfg: str, seed: int, dtype: str, want_bwd: bool, torch, T, syn
         gt, gq, gs = torch.zeros_like(t), torch.zeros_like(q), torch.zeros_like(s)
         grad_out = torch.zeros((rays.n, 4), dtype=torch.float32, device=dev)
         grads = (gp, gt, gq, gs, grad_out, target)
-    ev = {"march": []}
+    ev = {"march": [], "bwd": []}
     # the ABI structs hold raw device pointers: the step keeps their tensors alive
     keep = (t, q, s, payload, o, d)
 
@@ -206,7 +206,14 @@ def _frame_runner(cfg: str, seed: int, dtype: str, want_bwd: bool, torch, T, syn
             # photometric L2 loss (Sec. 3.3, lambda = 1): dL/dI = 2 (I - target) / R
             torch.sub(out[:, :3], target, out=grad_out[:, :3]).mul_(2.0 / rays.n)
             gp.zero_(), gt.zero_(), gq.zero_(), gs.zero_()
+            if time_march:
+                b0 = torch.cuda.Event(enable_timing=True)
+                b1 = torch.cuda.Event(enable_timing=True)
+                b0.record()
             T.raymarch_bwd(ctx, prims, bvh, rs, saved, grad_out, gp, gt, gq, gs)
+            if time_march:
+                b1.record()
+                ev["bwd"].append((b0, b1))
 
     info = {"scene": scene, "rays": rays, "ctx": ctx, "prims": prims, "bvh": bvh, "rs": rs, "ev": ev, "o": o, "d": d, "keep": keep,
             "payload_bytes": payload.numel() * payload.element_size(), "out": out,
@@ -762,6 +769,95 @@ def _serving(torch, T, synthetic, rates, n_req, seed=0):
             "rates": results, "budget_64MB_images": budget_run}
 
 
+def _gather_probe(torch, T):
+    """Ceilings of the march's voxel access pattern on this GPU (mvp_gather_probe):
+    8-corner gathers (FP32 16-byte and BF16 8-byte voxels) with L1-resident and
+    L2-resident footprints, and the adjoint's float4 reductions with an L2-resident
+    footprint. Each figure: the best of 5 launches timed with CUDA events on the
+    launching stream after one warm-up launch."""
+    import ctypes
+
+    from paper_2103_01954_gb300 import binding as B
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    M, steps = 16, 512
+    out = {"access_pattern": "8 corners per lane and sample, 8x4-pixel warp tiles, lanes 1/4 voxel apart, "
+                             "samples 2/3 voxel apart", "M": M, "footprint_l2_MB": 67}
+    sink = torch.zeros(1, dtype=torch.float32, device=dev)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def timed(payload, dtype, n, mode, footprint, grad=None):
+        acc = ctypes.c_int64(0)
+        args = (ctypes.c_void_p(payload.data_ptr()) if payload is not None else None, dtype, n, M, mode, footprint,
+                steps, ctypes.c_void_p(grad.data_ptr()) if grad is not None else None,
+                ctypes.c_void_p(sink.data_ptr()), ctypes.byref(acc), stream)
+        B.check(B.lib().mvp_gather_probe(*args), "mvp_gather_probe")
+        best = None
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            B.check(B.lib().mvp_gather_probe(*args), "mvp_gather_probe")
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return acc.value, best
+
+    n32 = 1024  # 1024 x 16^3 x 16 B = 67 MB (FP32); 2048 x 16^3 x 8 B = 67 MB (BF16)
+    p32 = torch.rand((n32, M, M, M, 4), dtype=torch.float32, device=dev)
+    for name, payload, dtype, n, vb in (("f32", p32, B.MVP_F32, n32, 16),
+                                        ("bf16", torch.rand((2 * n32, M, M, M, 4), device=dev).to(torch.bfloat16),
+                                         B.MVP_BF16, 2 * n32, 8)):
+        for fp, tag in ((0, "l1"), (1, "l2")):
+            acc, ms = timed(payload, dtype, n, 0, fp)
+            out[f"gather_{name}_{tag}_GBps"] = round(acc * vb / (ms * 1e-3) / 1e9, 1)
+        del payload
+    del p32
+    g = torch.zeros((n32, M, M, M, 4), dtype=torch.float32, device=dev)
+    acc, ms = timed(None, B.MVP_F32, n32, 1, 1, grad=g)
+    out["scatter_f32x4_l2_Gupdates_s"] = round(acc / (ms * 1e-3) / 1e9, 2)
+    del g
+    torch.cuda.empty_cache()
+    return out
+
+
+def _summary(variants, serving, probe):
+    """Every part of the metric as flat scalars (the record keeps config's scalars)."""
+    out = {}
+    for key, name in (("fwd_bf16", "fwd_bf16_mrays_s"), ("fwd_f16", "fwd_f16_mrays_s"),
+                      ("fwd_bwd_f32_512x32^3_4x512x512", "fwd_bwd_f32_512x32c_4x512x512_mrays_s"),
+                      ("fwd_f32_512x32^3", "fwd_f32_512x32c_mrays_s"), ("fwd_f32_32768x8^3", "fwd_f32_32768x8c_mrays_s"),
+                      ("fwd_bf16_32768x8^3", "fwd_bf16_32768x8c_mrays_s")):
+        if isinstance(variants.get(key), dict) and "value" in variants[key]:
+            out[name] = variants[key]["value"]
+    fb = variants.get("fwd_bwd_f32_512x32^3_4x512x512")
+    if fb:
+        out["fwd_bwd_backward_ms"] = fb["backward_ms"]
+        out["fwd_bwd_forward_ms"] = fb["forward_ms"]
+        out["backward_scatter_frac"] = fb["backward_roofline"]["frac"]
+    for k in ("bf16_over_f32", "e2e_bf16_over_f32"):
+        if k in variants:
+            out[k] = variants[k]
+    if isinstance(variants.get("fwd_bf16"), dict) and "gather_frac" in variants["fwd_bf16"]:
+        out["fwd_bf16_gather_frac"] = variants["fwd_bf16"]["gather_frac"]
+    for k, v in probe.items():
+        if isinstance(v, (int, float)):
+            out["probe_" + k] = v
+    if serving:
+        for rate, r in serving["rates"].items():
+            tag = rate.replace(".0_req_per_s", "rps").replace("_req_per_s", "rps")
+            out[f"serving_{tag}_requests"] = r["requests"]
+            out[f"serving_{tag}_p50_ms"] = r["p50_ms"]
+            out[f"serving_{tag}_p99_ms"] = r["p99_ms"]
+            out[f"serving_{tag}_mrays_s"] = r["mrays_per_s"]
+            out[f"serving_{tag}_one_at_a_time_f32_p50_ms"] = r["one_at_a_time_f32"]["p50_ms"]
+            out[f"serving_{tag}_one_at_a_time_f32_p99_ms"] = r["one_at_a_time_f32"]["p99_ms"]
+            out[f"serving_{tag}_one_at_a_time_f32_mrays_s"] = r["one_at_a_time_f32"]["mrays_per_s"]
+            if "served_f32_payload" in r:
+                out[f"serving_{tag}_served_f32_payload_mrays_s"] = r["served_f32_payload"]["mrays_per_s"]
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -798,15 +894,21 @@ def run_gpu(args):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s (FMA = 2)
     ncu = _ncu_record("k_march_f32")
-    achieved = FLOP_PER_EVAL * n_eval / (march_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
-                "frac": round(achieved / fp32_peak, 4), "traffic": ncu.get("dram_bytes_per_launch"),
-                "l1_wavefront_frac": ncu.get("l1_wavefront_frac"),
+    probe = _gather_probe(torch, T)
+    gather = GATHER_BYTES["f32"] * n_eval / (march_ms * 1e-3) / 1e9  # GB/s
+    g_peak = probe["gather_f32_l1_GBps"]
+    alu = FLOP_PER_EVAL * n_eval / (march_ms * 1e-3) / 1e12
+    roofline = {"bound": "gather", "achieved": round(gather, 1), "peak": g_peak, "unit": "GB/s",
+                "frac": round(gather / g_peak, 4), "traffic": ncu.get("dram_bytes_per_launch"),
+                "peak_kind": "measured: mvp_gather_probe, the march's 8-corner FP32 gathers, L1-resident",
+                "peak_l2_resident_GBps": probe["gather_f32_l2_GBps"],
+                "frac_of_l2_resident": round(gather / probe["gather_f32_l2_GBps"], 4),
                 "kernel": "k_march<f32>", "march_ms": round(march_ms, 4), "evaluations": n_eval,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
-                "gather_GBps": round(GATHER_BYTES["f32"] * n_eval / (march_ms * 1e-3) / 1e9, 1),
-                "gather_frac_of_l1_nominal": round(GATHER_BYTES["f32"] * n_eval / (march_ms * 1e-3) / 1e9 /
-                                                   (152 * 128 * sm_max * 1e6 / 1e9), 4),
+                "bytes_per_evaluation": GATHER_BYTES["f32"],
+                "l1_wavefront_frac": ncu.get("l1_wavefront_frac"),
+                "alu_achieved_TFLOPs": round(alu, 3), "alu_peak_TFLOPs": round(fp32_peak, 2),
+                "alu_frac": round(alu / fp32_peak, 4),
+                "alu_peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
                 "hbm_frac": (round(ncu["dram_bytes_per_launch"] / (march_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)
                              if ncu.get("dram_bytes_per_launch") and peaks.get("hbm_gbs") else None),
                 "hbm_peak_GBps": peaks.get("hbm_gbs"), "hbm_peak_kind": peak_kind}
@@ -864,12 +966,23 @@ def run_gpu(args):
         variants["fwd_f32_sequential"] = _sequential_blend(torch, T, synthetic, args, flush)
         variants["orbiting_camera"] = _orbit(torch, T, synthetic, args, flush)
         st, nr, inf = _frame_runner("diff_512x32^3_4x512x512", 0, "f32", True, torch, T, synthetic)
-        d = _time_steps(torch, st, args.steps, args.warmup, flush)
+        d = _time_steps(torch, st, args.steps, args.warmup, flush, time_march=True)
         inf["ctx"].sync()
         m = float(np.mean(d))
+        bwd_ms = float(np.mean([a.elapsed_time(b) for a, b in inf["ev"]["bwd"]]))
+        fwd_ms = float(np.mean([a.elapsed_time(b) for a, b in inf["ev"]["march"]]))
+        e_diff = int(T.raymarch_count(inf["ctx"], inf["prims"], inf["bvh"], inf["rs"]).sum().item())
+        inf["ctx"].sync()
+        upd = 8 * e_diff / (bwd_ms * 1e-3) / 1e9  # float4 corner reductions per second (G)
         variants["fwd_bwd_f32_512x32^3_4x512x512"] = {
             "value": round(nr / (m * 1e-3) / 1e6, 3), "unit": "Mrays/s", "ms_per_step": round(m, 4),
-            "workload": "diff_512x32^3_4x512x512", "step": "BVH + forward + L2 loss grad + backward (payload + pose)"}
+            "forward_ms": round(fwd_ms, 4), "backward_ms": round(bwd_ms, 4),
+            "workload": "diff_512x32^3_4x512x512", "step": "BVH + forward + L2 loss grad + backward (payload + pose)",
+            "backward_roofline": {"bound": "scatter (float4 reductions)", "evaluations": e_diff,
+                                  "achieved_Gupdates_s": round(upd, 2),
+                                  "peak_Gupdates_s": probe["scatter_f32x4_l2_Gupdates_s"],
+                                  "peak_kind": "measured: mvp_gather_probe mode 1, L2-resident footprint",
+                                  "frac": round(upd / probe["scatter_f32x4_l2_Gupdates_s"], 4)}}
         del st, inf
         torch.cuda.empty_cache()
         variants["fade_pack_bf16"] = _fade_pack(torch, T, synthetic, peaks)
@@ -878,6 +991,9 @@ def run_gpu(args):
         variants["vr_stereo_view_dependent_896x832"] = _vr_stereo(torch, T, synthetic, flush, view_dependent=True)
         if variants.get("fwd_bf16"):
             variants["bf16_over_f32"] = round(variants["fwd_bf16"]["value"] / value, 3)
+            gb = GATHER_BYTES["bf16"] * n_eval / (variants["fwd_bf16"]["march_ms"] * 1e-3) / 1e9
+            variants["fwd_bf16"]["gather_GBps"] = round(gb, 1)
+            variants["fwd_bf16"]["gather_frac"] = round(gb / probe["gather_bf16_l1_GBps"], 4)
         if variants.get("e2e_bf16") and result.get("e2e"):
             variants["e2e_bf16_over_f32"] = round(variants["e2e_bf16"]["value"] / result["e2e"]["value"], 3)
         result["variants"] = variants
@@ -887,6 +1003,7 @@ def run_gpu(args):
             torch.cuda.empty_cache()
         if not args.no_cpu:
             result["cpu_baseline"] = _cpu_baseline(args.cpu_seconds)
+        result["config"].update(_summary(variants, result.get("serving"), probe))
     if ws > 1:
         import torch.distributed as dist
 

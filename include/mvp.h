@@ -357,6 +357,26 @@ MVP_API mvp_status mvp_axis_angle_backward(mvp_ctx *ctx, const float *r, const f
 MVP_API mvp_status mvp_volume_prior(mvp_ctx *ctx, const float *s, int32_t n, float lambda, float *loss, float *g_s,
                                     mvp_stream stream);
 
+/* ------------------------------------------------ roofline probe */
+/* No counterpart in the paper: a measurement of the GPU, the ceiling that the march's
+ * and the adjoint's roofline fractions are taken against. Issues the voxel accesses of
+ * the march (mode 0: per lane and sample, loads of the 8 corner voxels of one cell of
+ * `payload` [n][M][M][M][4] in `dtype`) or of the adjoint (mode 1: a float4 reduction
+ * into each of the 8 corners of `grad`, FP32 [n][M][M][M][4]) in the march's coherence
+ * pattern (8x4-pixel warp tiles, neighbouring lanes a quarter voxel apart, consecutive
+ * samples two thirds of a voxel apart), with no other work, one wave of full blocks on
+ * every SM, `steps` samples per lane. footprint 0: each SM works inside one primitive
+ * (L1-resident after first touch); 1: warps move between all n primitives every 16
+ * samples (L2-resident when the array fits L2). sink (device float[1], mode 0) receives
+ * the sum of the loaded values; grad (mode 1) receives the reductions (contents are
+ * meaningless). *accesses (host, nullable) = voxel accesses of the launch (each 16 B
+ * FP32 or 8 B BF16/FP16). Arrays are device memory owned by the caller: payload 16-byte
+ * (FP32) or 8-byte aligned, grad 16-byte aligned. MVP_ERR_INVALID_ARG for bad sizes,
+ * modes or alignment. Asynchronous on `stream`; time it with events on that stream. */
+MVP_API mvp_status mvp_gather_probe(const void *payload, int32_t dtype, int32_t n, int32_t M, int32_t mode,
+                                    int32_t footprint, int32_t steps, float *grad, float *sink, int64_t *accesses,
+                                    mvp_stream stream);
+
 /* ------------------------------------------------ allocation-free render */
 /* No counterpart in the paper. For callers that cannot allocate device memory:
  * a plug-in inside a host application that owns every device allocation, a
@@ -369,7 +389,9 @@ MVP_API mvp_status mvp_volume_prior(mvp_ctx *ctx, const float *s, int32_t n, flo
  * (about 4 MB, held by every GPU that loads the library until the process exits).
  * Returns MVP_ERR_INVALID_ARG for more primitives than that (or any other bad
  * argument), before launching anything. The first call on a device looks up the
- * array's device address, so make it before any stream capture. Every call reuses
+ * array's device address, and so does the first call after that device's context
+ * was re-created (cudaDeviceReset, or the primary context released and retained
+ * again): make those calls before any stream capture. Every call reuses
  * the same array and it keeps the last call's contents; calls whose GPU work
  * overlaps (other streams or threads) race on it and must be serialised by the
  * caller. status_out (device int32, nullable) receives the kernels' status bits

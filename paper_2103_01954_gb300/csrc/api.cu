@@ -8,6 +8,8 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "march.cuh"
 #include "pack.cuh"
@@ -228,6 +230,51 @@ struct DeviceGuard {
 namespace mvp {
 // Lets other translation units of the library set the message mvp_last_error() returns.
 void record_error(const char *msg) { g_err = msg; }
+
+unsigned long long current_context_id() {
+  // cuCtxGetCurrent / cuCtxGetId through the runtime's driver entry points (the
+  // library links no driver library of its own); looked up once per process
+  using GetCurrent = int (*)(void **);  // CUresult is an int-sized enum; 0 = success
+  using GetId = int (*)(void *, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  });
+  if (!get_current || !get_id) return 0;
+  void *c = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&c) != 0 || !c || get_id(c, &id) != 0) return 0;
+  return id;
+}
+
+cudaError_t allow_dynamic_smem(const void *kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<const void *, unsigned long long>, size_t>> done;
+  const unsigned long long ctx = current_context_id();
+  if (ctx != 0) {
+    std::lock_guard<std::mutex> lk(mu);
+    for (const auto &d : done)
+      if (d.first.first == kernel && d.first.second == ctx && d.second >= bytes) return cudaSuccess;
+  }
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  const unsigned long long now = ctx ? ctx : current_context_id();  // the set-up may have created it
+  if (now != 0) {
+    std::lock_guard<std::mutex> lk(mu);
+    done.push_back({{kernel, now}, bytes});
+  }
+  return cudaSuccess;
+}
 int ctx_device(const mvp_ctx *ctx) { return ctx->device; }
 }  // namespace mvp
 

@@ -306,13 +306,8 @@ __global__ void k_pose_grads(const float *__restrict__ gmc, const Xform *__restr
 template <int DT, int CAP, int MT, bool SEQ = false>
 static cudaError_t launch_bwd_t(const BwdArgs &b, cudaStream_t st) {
   size_t smem = sizeof(TileShared<CAP>) * TILE_WARPS;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_backward<DT, CAP, MT, SEQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void *>(k_backward<DT, CAP, MT, SEQ>), smem);
+  if (e != cudaSuccess) return e;
   int64_t blocks = (b.m.geom.n_warp_tiles + TILE_WARPS - 1) / TILE_WARPS;
   if (blocks > 0) k_backward<DT, CAP, MT, SEQ><<<(unsigned)blocks, TILE_WARPS * 32, smem, st>>>(b);
   return cudaGetLastError();

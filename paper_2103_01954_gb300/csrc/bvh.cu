@@ -739,18 +739,14 @@ cudaError_t bvh_build(BvhBuffers &b, const float *t, const float *q, const float
   const int n_partial = (n + 255) / 256;
   if (n <= BVH_SORT1_N && (size_t)6 * n_partial <= (size_t)256 * G) {
     // mid-sized n: primitives with per-block bounds, then one block sorts
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaError_t e = cudaFuncSetAttribute(k_sort_one, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SORT1_SMEM);
-      if (e != cudaSuccess) return e;
-      attr_set = true;
-    }
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void *>(k_sort_one), SORT1_SMEM);
+    if (e != cudaSuccess) return e;
     float *partial = reinterpret_cast<float *>(b.counts);  // 6 floats per 256 primitives
     k_prims_partial<<<n_partial, 256, 0, st>>>(t, q, s, n, M, b.pose, b.xf, b.pbox, partial, status);
     // the rest of the chain is scheduled while its predecessor finishes (each kernel
     // waits for it before touching memory)
-    cudaError_t e = pdl_launch(k_sort_one, dim3(1), dim3(SORT1_THREADS), SORT1_SMEM, st, t, n,
-                               (const float *)partial, n_partial, b.scene, b.keys_a, b.vals_a, b.keys_b, b.vals_b);
+    e = pdl_launch(k_sort_one, dim3(1), dim3(SORT1_THREADS), SORT1_SMEM, st, t, n, (const float *)partial,
+                   n_partial, b.scene, b.keys_a, b.vals_a, b.keys_b, b.vals_b);
     if (e != cudaSuccess) return e;
   } else {
     k_bounds<<<1, 1024, 0, st>>>(t, n, b.scene);

@@ -50,6 +50,18 @@ inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// Host side (api.cu). Identity of the calling thread's current CUDA context: unique
+// for the life of the process (a context re-created after cudaDeviceReset gets a new
+// one); 0 when the thread has no current context.
+unsigned long long current_context_id();
+
+// Host side (api.cu). Lets `kernel` launch with `bytes` of dynamic shared memory in
+// the current context. The opt-in (cudaFuncAttributeMaxDynamicSharedMemorySize)
+// belongs to the kernel in one context, so it is remembered per (kernel, context)
+// under a mutex: each device a process drives, and a context re-created after a
+// reset, is opted in on its first launch there.
+cudaError_t allow_dynamic_smem(const void *kernel, size_t bytes);
+
 // Checked builds (-DMVP_CHECK_BOUNDS, the stand-in for a memory checker): an index
 // outside its array sets STATUS_BOUNDS and the access is skipped. Elsewhere the
 // check compiles to nothing.

@@ -148,13 +148,8 @@ __global__ void __launch_bounds__(1024) k_offsets(const int64_t *__restrict__ co
 template <int DT, int CAP, bool COUNT, int MT, bool SEQ = false>
 static cudaError_t launch_march_t(const MarchArgs &a, cudaStream_t st) {
   size_t smem = sizeof(TileShared<CAP>) * TILE_WARPS;
-  static bool attr_set = false;  // per instantiation; set once per process
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_march<DT, CAP, COUNT, MT, SEQ>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void *>(k_march<DT, CAP, COUNT, MT, SEQ>), smem);
+  if (e != cudaSuccess) return e;
   int64_t blocks = (a.geom.n_warp_tiles + TILE_WARPS - 1) / TILE_WARPS;
   if (blocks == 0) return cudaSuccess;
   return pdl_launch(k_march<DT, CAP, COUNT, MT, SEQ>, dim3((unsigned)blocks), dim3(TILE_WARPS * 32), smem, st, a);

@@ -47,10 +47,13 @@ constexpr size_t kBytes = align256(kOffRank + (size_t)kMaxPrims * sizeof(int));
 
 static __device__ __align__(256) unsigned char g_static_scratch[kBytes];
 
-// Device address of the array, looked up once per device with that device current.
+// Device address of the array, looked up once per device with that device current,
+// and again when the device's context is not the one the address was taken in (the
+// old address dies with its context, e.g. after cudaDeviceReset).
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char *g_addr[kMaxDevices] = {};
+unsigned long long g_ctx[kMaxDevices] = {};
 
 mvp_status reject(mvp_status s, const char *msg) {
   mvp::record_error(msg);  // reported by mvp_last_error()
@@ -87,11 +90,13 @@ extern "C" mvp_status mvp_raymarch_fwd_static(const mvp_prims *prims, const mvp_
   unsigned char *base;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    const unsigned long long ctx = mvp::current_context_id();
+    if (!g_addr[dev] || ctx == 0 || ctx != g_ctx[dev]) {
       void *p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+      cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);  // creates the context if there is none yet
       if (e != cudaSuccess || !p) return reject(MVP_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
       g_addr[dev] = static_cast<unsigned char *>(p);
+      g_ctx[dev] = mvp::current_context_id();
     }
     base = g_addr[dev];
   }

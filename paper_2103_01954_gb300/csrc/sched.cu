@@ -81,13 +81,8 @@ __global__ void __launch_bounds__(1024) k_tile_order(const unsigned int *__restr
 
 cudaError_t launch_tile_order(const unsigned int *cost, int64_t n, int *order, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tile_order, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ORDER_SMEM_KEYS);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void *>(k_tile_order), ORDER_SMEM_KEYS);
+  if (e != cudaSuccess) return e;
   const size_t smem = n <= ORDER_SMEM_KEYS ? (size_t)n : 0;
   k_tile_order<<<1, 1024, smem, st>>>(cost, n, order);
   return cudaGetLastError();

@@ -41,7 +41,7 @@ def test_definition_bar_rejects_planted_errors():
     with pytest.raises(AssertionError):
         definition_bar(bad, f64, "planted error above the cap")
     bad = img.copy()
-    bad[near[3:6], 2] += 2e-2  # near faces, over 1e-2 on more than 1 in 10^4 pixels
+    bad[near[3:20], 2] += 2e-2  # near faces, but over 1e-2 on more than 1 % of the near-face pixels
     with pytest.raises(AssertionError):
         definition_bar(bad, f64, "planted errors over 1e-2")
     bad = img.copy()
