@@ -94,6 +94,20 @@ __device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs
       const int64_t kbase = (int64_t)k * M2 * M;
       int held = -1;  // voxel (within the primitive) whose cell corners are held
       float4 c000, c001, c010, c011, c100, c101, c110, c111;
+      // the held cell's 8 corner shares of dL/d(rgba), summed over the lane's consecutive
+      // samples in that cell and reduced into g_payload once the lane leaves it
+      float4 s000, s001, s010, s011, s100, s101, s110, s111;
+      const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      s000 = s001 = s010 = s011 = s100 = s101 = s110 = s111 = zero4;
+      float4 *G = b.g_payload ? reinterpret_cast<float4 *>(b.g_payload) + kbase : nullptr;
+#define MVP_FLUSH(vox)                                                                                 \
+  {                                                                                                    \
+    float4 *g_ = G + (vox);                                                                            \
+    atomicAdd(g_, s000), atomicAdd(g_ + 1, s001), atomicAdd(g_ + M, s010), atomicAdd(g_ + M + 1, s011); \
+    atomicAdd(g_ + M2, s100), atomicAdd(g_ + M2 + 1, s101), atomicAdd(g_ + M2 + M, s110);             \
+    atomicAdd(g_ + M2 + M + 1, s111);                                                                  \
+    s000 = s001 = s010 = s011 = s100 = s101 = s110 = s111 = zero4;                                     \
+  }
       for (int it = 0; it < max_cnt; ++it) {
         const int i = lo + it;
         const bool in = it < cnt;
@@ -106,7 +120,7 @@ __device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs
         float fx = 0.0f, fy = 0.0f, fz = 0.0f;
         float4 gv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         int vo = -1;
-        if (in) {
+        {
           const float ti = sample_t(a.t_near, a.dt, i);
           const float x0 = fmaf(ti, L.d[0], L.o[0]);
           const float x1 = fmaf(ti, L.d[1], L.o[1]);
@@ -125,6 +139,7 @@ __device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs
           vo = iz * M2 + iy * M + ix;  // voxel within the primitive
           if (!MVP_IN_BOUNDS(vo >= 0 && vo + M2 + M + 1 < M2 * M, a.status)) continue;
           if (vo != held) {            // consecutive samples often stay in one cell
+            if (G && held >= 0) MVP_FLUSH(held);
             c000 = Voxel<DT>::load(pbase, vo);
             c001 = Voxel<DT>::load(pbase, vo + 1);
             c010 = Voxel<DT>::load(pbase, vo + M);
@@ -169,28 +184,30 @@ __device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs
             acc[5] = __ffma2_rn(make_float2(guy, guz), make_float2(1.0f, 1.0f), acc[5]);
           }
         }
-        if (in && b.g_payload) {
-          // the 8 corners of the cell get trilinear-weighted shares (float4 reductions)
-          float4 *G = reinterpret_cast<float4 *>(b.g_payload) + kbase + vo;
+        if (G) {
+          // this sample's trilinear-weighted shares of gv, added to the held cell's
           const float wx0 = 1.0f - fx, wy0 = 1.0f - fy, wz0 = 1.0f - fz;
           const float w00 = wy0 * wz0, w01 = fy * wz0, w10 = wy0 * fz, w11 = fy * fz;
           const float2 glo = lo2(gv), ghi = hi2(gv);
-#define MVP_SCATTER(off, WGT)                                                        \
-  {                                                                                  \
-    const float2 wg = splat2(WGT), l_ = __fmul2_rn(wg, glo), h_ = __fmul2_rn(wg, ghi); \
-    atomicAdd(G + (off), make_float4(l_.x, l_.y, h_.x, h_.y));                       \
+#define MVP_SHARE(S, WGT)                                                                \
+  {                                                                                      \
+    const float2 wg = splat2(WGT);                                                       \
+    const float2 l_ = __ffma2_rn(wg, glo, lo2(S)), h_ = __ffma2_rn(wg, ghi, hi2(S));     \
+    S = make_float4(l_.x, l_.y, h_.x, h_.y);                                             \
   }
-          MVP_SCATTER(0, wx0 * w00);
-          MVP_SCATTER(1, fx * w00);
-          MVP_SCATTER(M, wx0 * w01);
-          MVP_SCATTER(M + 1, fx * w01);
-          MVP_SCATTER(M2, wx0 * w10);
-          MVP_SCATTER(M2 + 1, fx * w10);
-          MVP_SCATTER(M2 + M, wx0 * w11);
-          MVP_SCATTER(M2 + M + 1, fx * w11);
-#undef MVP_SCATTER
+          MVP_SHARE(s000, wx0 * w00);
+          MVP_SHARE(s001, fx * w00);
+          MVP_SHARE(s010, wx0 * w01);
+          MVP_SHARE(s011, fx * w01);
+          MVP_SHARE(s100, wx0 * w10);
+          MVP_SHARE(s101, fx * w10);
+          MVP_SHARE(s110, wx0 * w11);
+          MVP_SHARE(s111, fx * w11);
+#undef MVP_SHARE
         }
       }
+      if (G && held >= 0) MVP_FLUSH(held);
+#undef MVP_FLUSH
       if (b.gmc) {
         float sums[12];
 #pragma unroll
@@ -220,7 +237,7 @@ __device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs
 // The tile schedule as in the frame kernel (its own cost record: the adjoint's
 // expensive tiles are not quite the forward's).
 #ifndef MVP_BWD_MINB
-#define MVP_BWD_MINB 4  // resident blocks per SM the adjoint is compiled for
+#define MVP_BWD_MINB 3  // resident blocks per SM the adjoint is compiled for
 #endif
 
 template <int DT, int CAP, int MT, bool SEQ>
