@@ -771,9 +771,11 @@ def _serving(torch, T, synthetic, rates, n_req, seed=0):
 
 def _gather_probe(torch, T):
     """Ceilings of the march's voxel access pattern on this GPU (mvp_gather_probe):
-    8-corner gathers (FP32 16-byte and BF16 8-byte voxels) with L1-resident and
-    L2-resident footprints, and the adjoint's float4 reductions with an L2-resident
-    footprint. Each figure: the best of 5 launches timed with CUDA events on the
+    8-corner gathers (FP32 16-byte and BF16 8-byte voxels; plain layout, and the
+    duplicated x-pair and xy-quad layouts that fetch a cell in 4 or 2 loads, and the
+    plain layout staged through shared memory per 4-sample chunk) with
+    L1-resident and L2-resident footprints, and the adjoint's float4 reductions with an
+    L2-resident footprint. Rates are algorithmic bytes (8 corners per evaluation). Each figure: the best of 5 launches timed with CUDA events on the
     launching stream after one warm-up launch."""
     import ctypes
 
@@ -804,15 +806,15 @@ def _gather_probe(torch, T):
         return acc.value, best
 
     n32 = 1024  # 1024 x 16^3 x 16 B = 67 MB (FP32); 2048 x 16^3 x 8 B = 67 MB (BF16)
-    p32 = torch.rand((n32, M, M, M, 4), dtype=torch.float32, device=dev)
-    for name, payload, dtype, n, vb in (("f32", p32, B.MVP_F32, n32, 16),
-                                        ("bf16", torch.rand((2 * n32, M, M, M, 4), device=dev).to(torch.bfloat16),
-                                         B.MVP_BF16, 2 * n32, 8)):
-        for fp, tag in ((0, "l1"), (1, "l2")):
-            acc, ms = timed(payload, dtype, n, 0, fp)
-            out[f"gather_{name}_{tag}_GBps"] = round(acc * vb / (ms * 1e-3) / 1e9, 1)
-        del payload
-    del p32
+    for name, tdt, dtype, vb in (("f32", torch.float32, B.MVP_F32, 16), ("bf16", torch.bfloat16, B.MVP_BF16, 8)):
+        for mode, per, lay in ((0, 1, ""), (2, 2, "_xpair"), (3, 4, "_xyquad"), (4, 1, "_smem_staged")):
+            n = n32 * 16 // (vb * per)  # the same 67 MB footprint for every layout
+            payload = torch.rand((n, M, M, M, per, 4), device=dev).to(tdt)
+            for fp, tag in ((0, "l1"), (1, "l2")):
+                acc, ms = timed(payload, dtype, n, mode, fp)
+                # algorithmic bytes: 8 corners of vb bytes per lane and sample
+                out[f"gather_{name}{lay}_{tag}_GBps"] = round(acc * vb / (ms * 1e-3) / 1e9, 1)
+            del payload
     g = torch.zeros((n32, M, M, M, 4), dtype=torch.float32, device=dev)
     acc, ms = timed(None, B.MVP_F32, n32, 1, 1, grad=g)
     out["scatter_f32x4_l2_Gupdates_s"] = round(acc / (ms * 1e-3) / 1e9, 2)
@@ -1077,7 +1079,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="headline figure only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--serving-requests", type=int, default=1000, help="requests per arrival rate (0: skip)")
+    ap.add_argument("--serving-requests", type=int, default=2000, help="requests per arrival rate (0: skip)")
     ap.add_argument("--serving-rates", default="50,100,200,400,1600", help="Poisson arrival rates, requests/s")
     ap.add_argument("--serving-only", action="store_true", help="run only the serving measurement")
     ap.add_argument("--profile", action="store_true", help="render --frames frames of --workload, no timing")

@@ -365,14 +365,20 @@ MVP_API mvp_status mvp_volume_prior(mvp_ctx *ctx, const float *s, int32_t n, flo
  * into each of the 8 corners of `grad`, FP32 [n][M][M][M][4]) in the march's coherence
  * pattern (8x4-pixel warp tiles, neighbouring lanes a quarter voxel apart, consecutive
  * samples two thirds of a voxel apart), with no other work, one wave of full blocks on
- * every SM, `steps` samples per lane. footprint 0: each SM works inside one primitive
+ * every SM, `steps` samples per lane. Modes 2 and 3 gather the same 8 corners from
+ * duplicated layouts: 2 = each voxel stored with its +x neighbour (`payload`
+ * [n][M][M][M][2][4], 4 loads per cell), 3 = each voxel with its +x, +y and +x+y
+ * neighbours ([n][M][M][M][2][2][4], 2 loads per cell). Mode 4 stages the plain
+ * layout through shared memory: per chunk of 4 samples a warp copies the box of
+ * voxels its lanes' cells span (up to 256 voxels; larger boxes are read directly)
+ * and reads the corners from there. footprint 0: each SM works inside one primitive
  * (L1-resident after first touch); 1: warps move between all n primitives every 16
  * samples (L2-resident when the array fits L2). sink (device float[1], mode 0) receives
  * the sum of the loaded values; grad (mode 1) receives the reductions (contents are
  * meaningless). *accesses (host, nullable) = voxel accesses of the launch (each 16 B
  * FP32 or 8 B BF16/FP16). Arrays are device memory owned by the caller: payload 16-byte
- * (FP32) or 8-byte aligned, grad 16-byte aligned. MVP_ERR_INVALID_ARG for bad sizes,
- * modes or alignment. Asynchronous on `stream`; time it with events on that stream. */
+ * (FP32) or 8-byte aligned (times 2 in mode 2 and 4 in mode 3), grad 16-byte aligned.
+ * MVP_ERR_INVALID_ARG for bad sizes, modes or alignment. Asynchronous on `stream`; time it with events on that stream. */
 MVP_API mvp_status mvp_gather_probe(const void *payload, int32_t dtype, int32_t n, int32_t M, int32_t mode,
                                     int32_t footprint, int32_t steps, float *grad, float *sink, int64_t *accesses,
                                     mvp_stream stream);

@@ -31,11 +31,12 @@ def _probe(payload, dtype, n, M, mode, footprint, steps, grad=None, sink=None):
 @pytest.mark.parametrize("dtype,tdt", [(B.MVP_F32, torch.float32), (B.MVP_BF16, torch.bfloat16),
                                        (B.MVP_F16, torch.float16)])
 @pytest.mark.parametrize("footprint", [0, 1])
-def test_probe_loads_every_access(dtype, tdt, footprint):
+@pytest.mark.parametrize("mode,per", [(0, 1), (2, 2), (3, 4), (4, 1)])
+def test_probe_loads_every_access(dtype, tdt, footprint, mode, per):
     n, M = 200, 16
-    payload = torch.ones((n, M, M, M, 4), dtype=tdt, device=DEV)
+    payload = torch.ones((n, M, M, M, per, 4), dtype=tdt, device=DEV)
     sink = torch.zeros(1, dtype=torch.float32, device=DEV)
-    st, acc = _probe(payload, dtype, n, M, 0, footprint, 8, sink=sink)
+    st, acc = _probe(payload, dtype, n, M, mode, footprint, 8, sink=sink)
     B.check(st, "probe")
     torch.cuda.synchronize()
     assert acc > 0 and acc % 8 == 0
@@ -60,8 +61,10 @@ def test_probe_rejects_bad_arguments():
     p = torch.ones((4, 8, 8, 8, 4), dtype=torch.float32, device=DEV)
     assert _probe(p, B.MVP_F32, 0, 8, 0, 0, 4, sink=sink)[0] == B.MVP_ERR_INVALID_ARG
     assert _probe(p, B.MVP_F32, 4, 1, 0, 0, 4, sink=sink)[0] == B.MVP_ERR_INVALID_ARG
-    assert _probe(p, B.MVP_F32, 4, 8, 2, 0, 4, sink=sink)[0] == B.MVP_ERR_INVALID_ARG
+    assert _probe(p, B.MVP_F32, 4, 8, 5, 0, 4, sink=sink)[0] == B.MVP_ERR_INVALID_ARG
     assert _probe(p, B.MVP_F32, 4, 8, 0, 0, 4)[0] == B.MVP_ERR_INVALID_ARG  # no sink
     assert _probe(None, B.MVP_F32, 4, 8, 1, 0, 4)[0] == B.MVP_ERR_INVALID_ARG  # no grad
     v = p.view(-1)[1:]  # 4-byte offset: misaligned for 16-byte voxels
     assert _probe(v, B.MVP_F32, 4, 8, 0, 0, 4, sink=sink)[0] == B.MVP_ERR_INVALID_ARG
+    v = p.view(-1)[4:]  # 16-byte aligned, but the pair layout's 32-byte elements are not
+    assert _probe(v, B.MVP_F32, 2, 8, 2, 0, 4, sink=sink)[0] == B.MVP_ERR_INVALID_ARG
