@@ -217,7 +217,7 @@ def _frame_runner(cfg: str, seed: int, dtype: str, want_bwd: bool, torch, T, syn
 
     info = {"scene": scene, "rays": rays, "ctx": ctx, "prims": prims, "bvh": bvh, "rs": rs, "ev": ev, "o": o, "d": d, "keep": keep,
             "payload_bytes": payload.numel() * payload.element_size(), "out": out,
-            "host": (scene, rays), "n_prims": int(scene.t.shape[0])}
+            "host": (scene, rays), "n_prims": int(scene.t.shape[0]), "M": int(scene.M)}
     return step, rays.n, info
 
 
@@ -837,6 +837,8 @@ def _summary(variants, serving, probe):
         out["fwd_bwd_backward_ms"] = fb["backward_ms"]
         out["fwd_bwd_forward_ms"] = fb["forward_ms"]
         out["backward_scatter_frac"] = fb["backward_roofline"]["frac"]
+        if fb["backward_roofline"].get("traffic_over_algorithmic") is not None:
+            out["backward_dram_over_algorithmic"] = fb["backward_roofline"]["traffic_over_algorithmic"]
     for k in ("bf16_over_f32", "e2e_bf16_over_f32"):
         if k in variants:
             out[k] = variants[k]
@@ -976,6 +978,9 @@ def run_gpu(args):
         e_diff = int(T.raymarch_count(inf["ctx"], inf["prims"], inf["bvh"], inf["rs"]).sum().item())
         inf["ctx"].sync()
         upd = 8 * e_diff / (bwd_ms * 1e-3) / 1e9  # float4 corner reductions per second (G)
+        # the adjoint's algorithmic bytes: payload read, its gradient read and written, 72 B per ray
+        alg = 3 * inf["n_prims"] * inf["M"] ** 3 * 16 + 72 * nr
+        nb = _ncu_record("k_backward_grouped_f32")
         variants["fwd_bwd_f32_512x32^3_4x512x512"] = {
             "value": round(nr / (m * 1e-3) / 1e6, 3), "unit": "Mrays/s", "ms_per_step": round(m, 4),
             "forward_ms": round(fwd_ms, 4), "backward_ms": round(bwd_ms, 4),
@@ -984,7 +989,12 @@ def run_gpu(args):
                                   "achieved_Gupdates_s": round(upd, 2),
                                   "peak_Gupdates_s": probe["scatter_f32x4_l2_Gupdates_s"],
                                   "peak_kind": "measured: mvp_gather_probe mode 1, L2-resident footprint",
-                                  "frac": round(upd / probe["scatter_f32x4_l2_Gupdates_s"], 4)}}
+                                  "frac": round(upd / probe["scatter_f32x4_l2_Gupdates_s"], 4),
+                                  "algorithmic_bytes": alg,
+                                  "traffic": nb.get("dram_bytes_per_launch"),
+                                  "traffic_over_algorithmic": (round(nb["dram_bytes_per_launch"] / alg, 3)
+                                                               if nb.get("dram_bytes_per_launch") else None),
+                                  "schedule": "primitive groups of a third of L2, replayed group after group"}}
         del st, inf
         torch.cuda.empty_cache()
         variants["fade_pack_bf16"] = _fade_pack(torch, T, synthetic, peaks)

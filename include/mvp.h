@@ -198,6 +198,16 @@ MVP_API size_t mvp_saved_bytes(int64_t n_rays);
  * order; a frame (mvp_build_bvh at an unchanged or smaller primitive count, then
  * mvp_raymarch_fwd) then only enqueues kernels and can be captured into a CUDA graph. */
 MVP_API mvp_status mvp_ctx_set_tile_schedule(mvp_ctx *ctx, int32_t enable);
+/* How mvp_raymarch_bwd walks the primitives (no counterpart in the paper: a memory
+ * schedule of the Sec. 3.2.2 replay). When the payload and its gradient together
+ * exceed twice `bytes`, the adjoint cuts the primitives into groups of consecutive BVH
+ * positions of about `bytes` each (at most 64 groups) and replays every warp tile once
+ * per group its rays meet, group after group, so that a group's payload and
+ * g_payload stay in L2 while all rays that touch them are replayed. bytes = 0 picks
+ * the size from the device's L2 (a third of it; the default); bytes < 0 never
+ * groups. Results equal the ungrouped replay up to the order of the float
+ * reductions. */
+MVP_API mvp_status mvp_ctx_set_bwd_group_bytes(mvp_ctx *ctx, int64_t bytes);
 /* Render: out_rgba [n][4] float32 device = (I + (1 - A) bg, A). `saved`
  * (device, mvp_saved_bytes(n) bytes, nullable) receives the per-ray state the
  * adjoint needs. `bvh` must have been built from the same prims. Rays are marched

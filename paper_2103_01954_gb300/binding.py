@@ -104,6 +104,7 @@ _SIGS = [
                                        c_int32, c_void_p]),
     ("mvp_bounds_checked", c_int32, []),
     ("mvp_ctx_set_tile_schedule", c_int32, [c_void_p, c_int32]),
+    ("mvp_ctx_set_bwd_group_bytes", c_int32, [c_void_p, c_int64]),
     ("mvp_axis_angle_to_quat", c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     ("mvp_axis_angle_backward", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     ("mvp_volume_prior", c_int32, [c_void_p, c_void_p, c_int32, c_float, c_void_p, c_void_p, c_void_p]),

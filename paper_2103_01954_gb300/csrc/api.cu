@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <string>
@@ -40,6 +41,7 @@ struct mvp_ctx {
   int *d_status = nullptr;  // device status word (STATUS_* bits)
   TileSched sched;          // the frame kernel's
   TileSched sched_bwd;      // the adjoint's
+  std::atomic<int64_t> bwd_group_bytes{0};  // mvp_ctx_set_bwd_group_bytes
 };
 
 struct mvp_bvh {
@@ -340,6 +342,12 @@ void mvp_ctx_destroy(mvp_ctx *ctx) {
   delete ctx;
 }
 
+mvp_status mvp_ctx_set_bwd_group_bytes(mvp_ctx *ctx, int64_t bytes) {
+  if (!ctx) return fail(MVP_ERR_INVALID_ARG, "ctx is NULL");
+  ctx->bwd_group_bytes.store(bytes);
+  return ok();
+}
+
 mvp_status mvp_ctx_set_tile_schedule(mvp_ctx *ctx, int32_t enable) {
   if (!ctx) return fail(MVP_ERR_INVALID_ARG, "ctx is NULL");
   for (TileSched *S : {&ctx->sched, &ctx->sched_bwd}) {
@@ -492,10 +500,41 @@ mvp_status mvp_raymarch_bwd(mvp_ctx *ctx, const mvp_prims *prims, mvp_bvh *bvh, 
   b.grad = grad_rgba;
   b.g_payload = g_payload;
   b.gmc = pose ? bvh->b.gmc : nullptr;
-  TileSched &S = ctx->sched_bwd;
-  std::lock_guard<std::mutex> lk(S.mu);
   const cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
+  // Group the primitives when the payload and its gradient exceed twice the group budget.
+  const int64_t vox = (int64_t)prims->M * prims->M * prims->M;
+  const int64_t per_prim = vox * (prims->dtype == MVP_F32 ? 16 : 8) + (g_payload ? vox * 16 : 0);
+  int64_t budget = ctx->bwd_group_bytes.load();
+  if (budget == 0) {
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->device) != cudaSuccess) cudaGetLastError();
+    budget = l2 > 0 ? l2 / 3 : 0;
+  }
+  const int n = prims->n;
+  if (budget > 0 && n > 1 && per_prim * n > 2 * budget && b.m.geom.n_warp_tiles <= 0x7fffffff / 64) {
+    mvp::BwdGroups gr;
+    gr.gsize = (int)std::max<int64_t>(1, std::min<int64_t>(n, budget / per_prim));
+    if ((n + gr.gsize - 1) / gr.gsize > 64) gr.gsize = (n + 63) / 64;
+    gr.n_groups = (n + gr.gsize - 1) / gr.gsize;
+    gr.range = reinterpret_cast<const int2 *>(bvh->b.parent);
+    // stream-ordered scratch: mask, work list, group offsets, work counter
+    const int64_t nt = b.m.geom.n_warp_tiles;
+    const size_t bytes = (size_t)nt * 8 + (size_t)nt * gr.n_groups * 4 + (size_t)(gr.n_groups + 2) * 4;
+    char *scratch = nullptr;
+    if ((e = cudaMallocAsync(&scratch, bytes, st)) != cudaSuccess) return cuda_fail(e, "adjoint group scratch");
+    gr.mask = reinterpret_cast<unsigned long long *>(scratch);
+    gr.items = reinterpret_cast<int *>(scratch + (size_t)nt * 8);
+    gr.goff = gr.items + (size_t)nt * gr.n_groups;
+    gr.work = gr.goff + gr.n_groups + 1;
+    e = mvp::launch_backward(b, prims->t, prims->q, prims->s, g_t, g_q, g_s, st, &gr);
+    const cudaError_t f = cudaFreeAsync(scratch, st);
+    if (e != cudaSuccess) return cuda_fail(e, "grouped backward launch");
+    if (f != cudaSuccess) return cuda_fail(f, "adjoint group scratch");
+    return ok();
+  }
+  TileSched &S = ctx->sched_bwd;
+  std::lock_guard<std::mutex> lk(S.mu);
   const bool use = sched_begin(S, b.m, st, e);
   if (e != cudaSuccess) return cuda_fail(e, "tile schedule wait");
   e = mvp::launch_backward(b, prims->t, prims->q, prims->s, g_t, g_q, g_s, st);

@@ -14,14 +14,18 @@
 // coordinate) times p = x - t_k and dL/du itself in registers; one warp reduction
 // per entry adds those 12 sums to the primitive's accumulator. A per-primitive
 // kernel then maps them to dL/dt, dL/dq, dL/ds through u = diag(h/s) R^T p + h.
+#include <algorithm>
+
 #include "march.cuh"
 
 namespace mvp {
 
 // The adjoint of one warp tile whose lane ray is L (SEQ: the forward blended the
-// saturating samples in BVH order).
-template <int DT, int CAP, int MT, bool SEQ>
-__device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs &b, const LaneRay &L) {
+// saturating samples in BVH order; RANGED: only the primitives at the BVH positions
+// of lr, the rest of the tile's work being another call's).
+template <int DT, int CAP, int MT, bool SEQ, bool RANGED = false>
+__device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs &b, const LaneRay &L,
+                                              LeafRange lr = LeafRange{nullptr, 0, 0}) {
   const MarchArgs &a = b.m;
   const int lane = threadIdx.x & 31;
   const bool valid = L.r >= 0;
@@ -61,9 +65,9 @@ __device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs
   int w0 = 0, wlen = a.n_steps, skip = 0;
   while (w0 <= max_last) {
     int w1 = min(a.n_steps, w0 + wlen);
-    int ne = build_window<CAP>(sh, a.nodes, a.pose, a.xf, reinterpret_cast<const char *>(a.payload), prim_bytes,
-                               a.n_prims, L, valid ? i_last : -1, a.t_near, a.t_far, a.dt, a.n_steps, w0, w1,
-                               skip, a.status);
+    int ne = build_window<CAP, RANGED>(sh, a.nodes, a.pose, a.xf, reinterpret_cast<const char *>(a.payload),
+                                       prim_bytes, a.n_prims, L, valid ? i_last : -1, a.t_near, a.t_far, a.dt,
+                                       a.n_steps, w0, w1, skip, a.status, lr);
     if (ne == WINDOW_STACK) {
       if (lane == 0) atomicOr(a.status, STATUS_CAPACITY);
       return;
@@ -271,6 +275,137 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, MVP_BWD_MINB) k_backward(BwdA
   }
 }
 
+// ------------------------------------------------------------------ primitive groups
+// When the payload and its gradient outgrow L2, the four cameras' tiles of the
+// differentiation workload would each sweep them from DRAM. The grouped adjoint
+// instead cuts the primitives into groups of consecutive BVH positions (spatially
+// compact, each sized to stay in L2 with its gradient) and replays every tile once per
+// group it meets, group after group, so a group's payload and g_payload lines are
+// read and written back about once.
+
+// Shared memory of the group-mask pass: the traversal's buffers only.
+struct TraverseShared {
+  Packet pk;
+  int stack[STACK];
+  int cand[CBUF];
+};
+
+// mask[t] = the groups (bit g: BVH positions [g gsize, (g+1) gsize)) whose primitives
+// tile t's rays may meet up to their last live sample: one traversal of the tile's
+// packet, each candidate kept if its oriented box passes the packet test. A tile whose
+// traversal overflows the stack gets every group, so its replay reports the overflow.
+__global__ void __launch_bounds__(TILE_WARPS * 32) k_bwd_groups(BwdArgs b, int gsize, int n_groups,
+                                                                unsigned long long *__restrict__ mask) {
+  __shared__ TraverseShared shm[TILE_WARPS];
+  const MarchArgs &a = b.m;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  TraverseShared &sh = shm[warp];
+  const int64_t slot = (int64_t)blockIdx.x * TILE_WARPS + warp;
+  if (slot >= a.geom.n_warp_tiles) return;
+  LaneRay L;
+  load_lane_ray(L, a.o, a.d, tile_ray(a.geom, slot, lane));
+  const bool valid = L.r >= 0;
+  const int i_last = valid ? b.saved[L.r].i_last : -1;
+  const int max_last = __reduce_max_sync(FULL, i_last);
+  unsigned long long m = 0;
+  if (max_last >= 0 && a.n_prims > 0 && a.n_steps > 0) {
+    make_packet(sh.pk, valid, L.o, L.d, a.t_far);
+    const float ta = sample_t(a.t_near, a.dt, 0), tb = sample_t(a.t_near, a.dt, min(max_last, a.n_steps - 1));
+    const float slack = 1.0e-5f * (fabsf(ta) + fabsf(tb)) + 1.0e-30f;
+    auto emit = [&](int nc) -> bool {
+      for (int c = lane; c < nc; c += 32) {
+        const int k = sh.cand[c];
+        const float4 *qa = reinterpret_cast<const float4 *>(a.pose + k);
+        Pose Pk;
+        Pk.p0 = __ldg(qa);
+        Pk.p1 = __ldg(qa + 1);
+        Pk.p2 = __ldg(qa + 2);
+        Pk.p3 = __ldg(qa + 3);
+        if (packet_hits_obb(sh.pk, Pk, ta - slack, tb + slack)) {
+          const int g = __ldg(a.rank + k) / gsize;
+          if (MVP_IN_BOUNDS(g >= 0 && g < n_groups, a.status)) m |= 1ull << g;
+        }
+      }
+      __syncwarp();
+      return true;
+    };
+    if (!traverse_tile(sh, a.nodes, a.n_prims, ta - slack, tb + slack, emit, a.status))
+      m = n_groups >= 64 ? ~0ull : (1ull << n_groups) - 1ull;
+  }
+  const unsigned lo = __reduce_or_sync(FULL, (unsigned)m), hi = __reduce_or_sync(FULL, (unsigned)(m >> 32));
+  if (lane == 0) mask[slot] = ((unsigned long long)hi << 32) | lo;
+}
+
+// The work list, group by group: items[goff[g] .. goff[g+1]) are the tiles of group g
+// (goff[G] = the total). Also clears the grouped adjoint's work counter. One block.
+constexpr int ITEMS_THREADS = 1024;
+__global__ void __launch_bounds__(ITEMS_THREADS) k_bwd_items(const unsigned long long *__restrict__ mask,
+                                                             int64_t n_tiles, int n_groups, int *__restrict__ items,
+                                                             int *__restrict__ goff, int *__restrict__ work) {
+  __shared__ int cnt[64], cur[64];
+  const int tid = threadIdx.x;
+  if (tid < 64) cnt[tid] = 0;
+  __syncthreads();
+  for (int64_t t = tid; t < n_tiles; t += ITEMS_THREADS) {
+    unsigned long long m = mask[t];
+    while (m) {
+      atomicAdd(&cnt[__ffsll((long long)m) - 1], 1);
+      m &= m - 1;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int g = 0; g < n_groups; ++g) {
+      goff[g] = run;
+      cur[g] = run;
+      run += cnt[g];
+    }
+    goff[n_groups] = run;
+    *work = 0;
+  }
+  __syncthreads();
+  for (int64_t t = tid; t < n_tiles; t += ITEMS_THREADS) {
+    unsigned long long m = mask[t];
+    while (m) {
+      items[atomicAdd(&cur[__ffsll((long long)m) - 1], 1)] = (int)t;
+      m &= m - 1;
+    }
+  }
+}
+
+// The grouped adjoint: persistent warps take (tile, group) items in list order (a
+// work counter), so the groups are replayed one after another across the GPU; each
+// item replays its tile against its group's primitives only.
+template <int DT, int CAP, int MT, bool SEQ>
+__global__ void __launch_bounds__(TILE_WARPS * 32, MVP_BWD_MINB)
+    k_backward_grouped(BwdArgs b, const int *__restrict__ items, const int *__restrict__ goff, int n_groups,
+                       int gsize, int *__restrict__ work, const int2 *__restrict__ range) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const MarchArgs &a = b.m;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  TileShared<CAP> &sh = reinterpret_cast<TileShared<CAP> *>(smem_raw)[warp];
+  const int total = goff[n_groups];
+  while (true) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(work, 1);
+    item = __shfl_sync(FULL, item, 0);
+    if (item >= total) break;
+    // the group of the item: the last g with goff[g] <= item (goff ascends, goff[0] = 0)
+    const unsigned m0 = __ballot_sync(FULL, lane < n_groups && goff[lane] <= item);
+    const unsigned m1 = __ballot_sync(FULL, lane + 32 < n_groups && goff[lane + 32] <= item);
+    const int g = __popc(m0) + __popc(m1) - 1;
+    const int tile = items[item];
+    if (!MVP_IN_BOUNDS(tile >= 0 && tile < a.geom.n_warp_tiles && g >= 0, a.status)) continue;
+    LaneRay L;
+    load_lane_ray(L, a.o, a.d, tile_ray(a.geom, tile, lane));
+    if (__ballot_sync(FULL, L.r >= 0) == 0) continue;
+    const LeafRange lr{range, g * gsize, min(a.n_prims, (g + 1) * gsize)};
+    backward_tile<DT, CAP, MT, SEQ, true>(sh, b, L, lr);
+    __syncwarp();
+  }
+}
+
 // Map the 12 accumulators of each primitive to pose gradients (+=):
 // u = Mx p + h with Mx_jm = h R_mj / s_j and p = x - t, A_jm = sum dL/du_j p_m,
 // g_j = sum dL/du_j:  dL/dt_m = -sum_j Mx_jm g_j;  dL/dR_mj = A_jm h / s_j;
@@ -330,9 +465,39 @@ static cudaError_t launch_bwd_t(const BwdArgs &b, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int DT, int CAP, int MT, bool SEQ = false>
+static cudaError_t launch_bwd_grouped_t(const BwdArgs &b, const BwdGroups &gr, cudaStream_t st) {
+  const void *k = reinterpret_cast<const void *>(k_backward_grouped<DT, CAP, MT, SEQ>);
+  const size_t smem = sizeof(TileShared<CAP>) * TILE_WARPS;
+  cudaError_t e = allow_dynamic_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_grouped<DT, CAP, MT, SEQ>,
+                                                         TILE_WARPS * 32, smem)) != cudaSuccess)
+    return e;
+  if (per_sm < 1) per_sm = 1;
+  // one block per resident slot, no more blocks than items could use
+  const int64_t need = (b.m.geom.n_warp_tiles * gr.n_groups + TILE_WARPS - 1) / TILE_WARPS;
+  const int64_t blocks = std::min<int64_t>((int64_t)sms * per_sm, std::max<int64_t>(need, 1));
+  k_backward_grouped<DT, CAP, MT, SEQ><<<(unsigned)blocks, TILE_WARPS * 32, smem, st>>>(
+      b, gr.items, gr.goff, gr.n_groups, gr.gsize, gr.work, gr.range);
+  return cudaGetLastError();
+}
+
 template <int DT>
-static cudaError_t launch_bwd_m(const BwdArgs &b, cudaStream_t st) {
+static cudaError_t launch_bwd_m(const BwdArgs &b, const BwdGroups *gr, cudaStream_t st) {
   // the sequential rule's adjoint: one generic-M kernel per payload type
+  if (gr) {
+    if (b.m.sequential) return launch_bwd_grouped_t<DT, MARCH_CAP, 0, true>(b, *gr, st);
+    switch (b.m.M) {
+      case 8: return launch_bwd_grouped_t<DT, MARCH_CAP, 8>(b, *gr, st);
+      case 16: return launch_bwd_grouped_t<DT, MARCH_CAP, 16>(b, *gr, st);
+      case 32: return launch_bwd_grouped_t<DT, MARCH_CAP, 32>(b, *gr, st);
+      default: return launch_bwd_grouped_t<DT, MARCH_CAP, 0>(b, *gr, st);
+    }
+  }
   if (b.m.sequential) return launch_bwd_t<DT, MARCH_CAP, 0, true>(b, st);
   switch (b.m.M) {
     case 8: return launch_bwd_t<DT, MARCH_CAP, 8>(b, st);
@@ -343,14 +508,21 @@ static cudaError_t launch_bwd_m(const BwdArgs &b, cudaStream_t st) {
 }
 
 cudaError_t launch_backward(const BwdArgs &b, const float *t, const float *q, const float *s, float *g_t,
-                            float *g_q, float *g_s, cudaStream_t st) {
+                            float *g_q, float *g_s, cudaStream_t st, const BwdGroups *gr) {
   (void)t;
   if (b.gmc) cudaMemsetAsync(b.gmc, 0, sizeof(float) * 12 * (size_t)b.m.n_prims, st);
   cudaError_t e = cudaSuccess;
+  if (gr) {
+    const int64_t nt = b.m.geom.n_warp_tiles;
+    k_bwd_groups<<<(unsigned)((nt + TILE_WARPS - 1) / TILE_WARPS), TILE_WARPS * 32, 0, st>>>(b, gr->gsize, gr->n_groups,
+                                                                                         gr->mask);
+    k_bwd_items<<<1, ITEMS_THREADS, 0, st>>>(gr->mask, nt, gr->n_groups, gr->items, gr->goff, gr->work);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   switch (b.m.dtype) {
-    case MVP_F32: e = launch_bwd_m<MVP_F32>(b, st); break;
-    case MVP_BF16: e = launch_bwd_m<MVP_BF16>(b, st); break;
-    case MVP_F16: e = launch_bwd_m<MVP_F16>(b, st); break;
+    case MVP_F32: e = launch_bwd_m<MVP_F32>(b, gr, st); break;
+    case MVP_BF16: e = launch_bwd_m<MVP_BF16>(b, gr, st); break;
+    case MVP_F16: e = launch_bwd_m<MVP_F16>(b, gr, st); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;

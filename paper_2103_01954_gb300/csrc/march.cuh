@@ -66,6 +66,19 @@ struct BwdArgs {
   float *gmc;              // [n][12] accumulators or null
 };
 
+// The grouped adjoint's primitive groups (consecutive BVH positions, gsize each) and
+// its scratch: per warp tile the groups it meets (mask), the (tile, group) work list
+// (items, goff[n_groups + 1]) and the work counter. range = the BVH's internal-node
+// leaf ranges.
+struct BwdGroups {
+  int gsize = 0, n_groups = 0;  // n_groups <= 64
+  unsigned long long *mask = nullptr;  // [n_warp_tiles]
+  int *items = nullptr;                // [n_warp_tiles * n_groups]
+  int *goff = nullptr;                 // [n_groups + 1]
+  int *work = nullptr;                 // [1]
+  const int2 *range = nullptr;         // [n_prims - 1]
+};
+
 cudaError_t launch_march(const MarchArgs &a, cudaStream_t st);
 // order = the n warp tiles by descending cost bucket (a permutation of 0..n-1,
 // whatever cost holds): the next frame's schedule, heaviest tiles first.
@@ -74,7 +87,8 @@ void record_error(const char *msg);
 int ctx_device(const mvp_ctx *ctx);
 cudaError_t launch_hits(const HitArgs &a, int64_t *counts, cudaStream_t st);
 cudaError_t launch_hits_fill(const HitArgs &a, cudaStream_t st);
+// gr (nullable): replay the tiles group by group (the BwdGroups scratch is the caller's)
 cudaError_t launch_backward(const BwdArgs &a, const float *t, const float *q, const float *s, float *g_t,
-                            float *g_q, float *g_s, cudaStream_t st);
+                            float *g_q, float *g_s, cudaStream_t st, const BwdGroups *gr = nullptr);
 
 }  // namespace mvp

@@ -201,12 +201,22 @@ struct TileShared {
   unsigned int clk;  // the frame kernel's tile start (clock), for its tile schedule
 };
 
+// Leaves of a contiguous range of BVH positions [r0, r1): the adjoint's primitive
+// groups. range[i] is internal node i's sorted leaf range [first, last]; leaf node
+// n-1+j holds the primitive at position j.
+struct LeafRange {
+  const int2 *range;
+  int r0, r1;
+};
+
 // Traverse the BVH for the packet over [ta, tb]. Candidate leaves (primitive ids)
 // are passed to `emit(nc)` in batches of up to CBUF via sh.cand; emit returns false
-// to abort. Returns false on stack overflow or an aborted emit.
-template <class SH, class Emit>
+// to abort. Returns false on stack overflow or an aborted emit. RANGED: only nodes
+// whose leaves meet the LeafRange are visited.
+template <bool RANGED = false, class SH, class Emit>
 __device__ __forceinline__ bool traverse_tile(SH &sh, const Node *__restrict__ nodes, int n_prims, float ta,
-                                              float tb, Emit &&emit, int *status = nullptr) {
+                                              float tb, Emit &&emit, int *status = nullptr,
+                                              LeafRange lr = LeafRange{nullptr, 0, 0}) {
   const Packet &P = sh.pk;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -221,6 +231,11 @@ __device__ __forceinline__ bool traverse_tile(SH &sh, const Node *__restrict__ n
       int node = lane < take ? sh.stack[sp + lane] : -1;
       __syncwarp();
       if (node >= 0 && !MVP_IN_BOUNDS(node < 2 * n_prims - 1, status)) node = -1;
+      if (RANGED && node >= 0) {
+        const int2 span = node >= n_prims - 1 ? make_int2(node - (n_prims - 1), node - (n_prims - 1))
+                                              : __ldg(lr.range + node);
+        if (span.x >= lr.r1 || span.y < lr.r0) node = -1;
+      }
       bool pass = false, leaf = false;
       int l = 0, r = 0;
       if (node >= 0) {
@@ -278,18 +293,19 @@ __device__ __forceinline__ void load_lane_ray(LaneRay &L, const float *__restric
 }
 
 // Build the window's primitive list for samples [w0, w1): every traversal
-// candidate that some lane's exact slab interval meets at a sample of the window
-// with index <= lane_last (the lane's last live sample). The first `skip` such
-// primitives (in the fixed traversal order) are passed over. Returns the number of
-// entries; WINDOW_FULL if more than CAP remain after the skipped ones (the list
-// then holds the first CAP of them, ready to use); WINDOW_STACK if the traversal
-// stack overflowed.
-template <int CAP>
+// candidate (RANGED: in the LeafRange) that some lane's exact slab interval meets at
+// a sample of the window with index <= lane_last (the lane's last live sample). The
+// first `skip` such primitives (in the fixed traversal order) are passed over.
+// Returns the number of entries; WINDOW_FULL if more than CAP remain after the
+// skipped ones (the list then holds the first CAP of them, ready to use);
+// WINDOW_STACK if the traversal stack overflowed.
+template <int CAP, bool RANGED = false>
 __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__restrict__ nodes,
                                             const Pose *__restrict__ pose, const Xform *__restrict__ xf,
                                             const char *payload, int64_t prim_bytes, int n_prims,
                                             const LaneRay &L, int lane_last, float t_near, float t_far, float dt,
-                                            int n_steps, int w0, int w1, int skip = 0, int *status = nullptr) {
+                                            int n_steps, int w0, int w1, int skip = 0, int *status = nullptr,
+                                            LeafRange lr = LeafRange{nullptr, 0, 0}) {
   const int lane = threadIdx.x & 31;
   float ta = sample_t(t_near, dt, w0);
   float tb = sample_t(t_near, dt, w1 - 1);
@@ -377,7 +393,7 @@ __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__r
     }
     return true;
   };
-  bool ok = traverse_tile(sh, nodes, n_prims, ta - slack, tb + slack, emit, status);
+  bool ok = traverse_tile<RANGED>(sh, nodes, n_prims, ta - slack, tb + slack, emit, status, lr);
   __syncwarp();
   if (!ok && !full) return WINDOW_STACK;
   // the entries' march transforms and payload pointers, loaded in parallel

@@ -77,6 +77,10 @@ class Context:
         """Heaviest tiles of the last frame first (default), or the plain tile order."""
         B.check(B.lib().mvp_ctx_set_tile_schedule(self.handle, 1 if enable else 0), "mvp_ctx_set_tile_schedule")
 
+    def set_bwd_group_bytes(self, nbytes: int):
+        """Adjoint primitive-group size in bytes (0: a third of L2, the default; < 0: never group)."""
+        B.check(B.lib().mvp_ctx_set_bwd_group_bytes(self.handle, int(nbytes)), "mvp_ctx_set_bwd_group_bytes")
+
     def close(self):
         if self.handle:
             B.lib().mvp_ctx_destroy(self.handle)

@@ -101,6 +101,12 @@ def run() -> dict:
     cam = synthetic.look_at_camera((0.3, -0.2, -3.0), 20, 12, 16.0)
     rays = synthetic.make_rays([cam], 1.0, 5.0, 0.02)
     frame("stack150", _stack(150, 3), rays, grads=True)  # window splitting and the overflow path
+    # the adjoint replayed primitive group by primitive group (mask, work list, persistent replay)
+    ctx.set_bwd_group_bytes(1)
+    frame("stack150_grouped", _stack(150, 3), rays, grads=True)
+    sc, rays_s, _ = synthetic.make_config("small_512x8^3_96x128", 1)
+    frame("small512_seq_grouped", sc, rays_s, sequential=True, grads=True)
+    ctx.set_bwd_group_bytes(0)
     # decode-side epilogues
     rng = np.random.default_rng(5)
     rgb = up(rng.uniform(0, 1, (64, 8, 8, 8, 3)).astype(np.float32))

@@ -186,3 +186,35 @@ def test_tile_schedule_keeps_gradients():
         assert np.array_equal(out, out0)
         for k in G0:
             assert _rel(G[k], G0[k].astype(np.float64)) <= 1e-5, k
+
+
+# --------------------------------------------------------------------------- grouped adjoint
+@pytest.mark.parametrize("cfg,dtype,sequential,budget", [
+    ("diff_small_64x8^3_2x48x40", torch.float32, False, 40_000),    # 16 KB per primitive: 2 per group
+    ("diff_small_64x8^3_2x48x40", torch.float32, False, 1),         # one primitive per group, 64 groups
+    ("small_4096x16^3_83x128", torch.float32, False, 1),            # capped at 64 groups of 64
+    ("small_4096x16^3_83x128", torch.bfloat16, False, 8_000_000),   # 96 KB per primitive: 50 groups
+    ("small_512x8^3_96x128", torch.float32, True, 300_000),         # sequential blending's adjoint, 29 groups
+])
+def test_grouped_adjoint_equals_ungrouped(cfg, dtype, sequential, budget):
+    """The adjoint replayed primitive group by primitive group (mvp_ctx_set_bwd_group_bytes)
+    against the one-pass replay: every gradient equal up to the order of the float
+    reductions, and the payload gradient against the oracle's adjoint."""
+    sc, rays, _ = synthetic.make_config(cfg, 2)
+    dv = Dev(sc, rays, payload_dtype=dtype)
+    if sequential:
+        dv.rs = T.rays_struct(dv.o, dv.d, sequential=True, **dv.params)
+    dv.build()
+    g = np.random.default_rng(11).standard_normal((rays.n, 4))
+    dv.ctx.set_bwd_group_bytes(-1)
+    _, plain = _gpu_grads(dv, g)
+    dv.ctx.set_bwd_group_bytes(budget)
+    _, grouped = _gpu_grads(dv, g)
+    for key in plain:
+        scale = np.abs(plain[key]).max()
+        err = np.abs(grouped[key].astype(np.float64) - plain[key]).max() / max(scale, 1e-30)
+        print(cfg, key, "grouped vs one pass", err)
+        assert err <= 1e-5, (key, err)
+    if dtype == torch.float32 and not sequential:
+        R = oracle.backward(sc, rays, g.astype(np.float32).astype(np.float64), F32M)
+        assert _rel(grouped["g_payload"], R["g_payload"]) <= 1e-3
