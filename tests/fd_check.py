@@ -235,6 +235,12 @@ def check(prob, whole_grads, grad_of_rays, params, label="", h=H):
                      plain, cond / max(abs(fd), 1e-300)))
     errs, fracs = np.asarray(errs), np.asarray(fracs)
     plains = np.asarray([r[8] for r in rows])
+    from parity_rules import REPORT
+
+    REPORT.append(("fd", label, {"params": len(params), "err_max": float(errs.max()),
+                                 "plain_c9_max": float(plains.max()), "plain_c9_ok": int((plains <= TOL).sum()),
+                                 "kinked": sum(r[5] for r in rows), "near_kink": sum(r[7] for r in rows),
+                                 "rays": sum(r[6] for r in rows)}))
     print(f"FD check {label}: {len(params)} parameters, error max {errs.max():.3e} median "
           f"{np.median(errs):.3e}; plain C9 (no conditioning floor) max {plains.max():.3e}, "
           f"{int((plains <= TOL).sum())} of {len(params)} within {TOL}; rays straddling a kink: "

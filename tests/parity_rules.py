@@ -27,6 +27,10 @@ from __future__ import annotations
 
 import numpy as np
 
+# Every check's counts, in the order the checks ran (tests/conftest.py prints a summary of
+# them at the end of the session, so they reach a quiet run's output).
+REPORT: list = []
+
 BAND = 2e-4      # per-channel parity band
 CAP = 1e-2       # largest channel error allowed off the faces
 NEAR_FACE_CAP = 0.1  # largest channel error allowed on a near-face pixel
@@ -55,6 +59,7 @@ def definition_bar(img, ref, label: str = "", min_frac: float = 0.999):
     assert st["max"] <= NEAR_FACE_CAP, (label, st)
     assert st["px_over_1e-2"] <= NEAR_FACE_OVER_CAP_SHARE * st["px_near_face"], (label, st)
     assert st["px_over_1e-2"] <= OVER_CAP_RATE * st["rays"], (label, st)
+    REPORT.append(("image", label, st))  # passed checks only
     return st
 
 
@@ -134,6 +139,7 @@ def hit_sets_vs_f64(gpu_lists, f64_lists, scene, rays, label: str = ""):
     assert np.all(dep_g - 1.0 < GRAZE_Y), (label, "GPU-only pairs that miss the box by more than the band", st)
     assert np.all(1.0 - dep_o < GRAZE_Y), (label, "FP64 hits the GPU drops that are not grazing", st)
     assert st["max_interval_diff_local"] <= GRAZE_Y, (label, st)
+    REPORT.append(("hits", label, st))  # passed checks only
     return st
 
 

@@ -27,6 +27,21 @@ def _rel(g, ref):
     return float(np.abs(np.asarray(g, np.float64) - ref).max() / max(np.abs(ref).max(), 1e-30))
 
 
+def _per_element(G, R, label):
+    """Per-element relative error |g - g_ref| / max(|g_ref|, 1e-3 max|g_ref|) of each
+    tensor (reported beside the per-tensor figure; the session summary prints it)."""
+    from parity_rules import REPORT
+
+    st = {}
+    for key in G:
+        ref = np.asarray(R[key], np.float64)
+        e = np.abs(np.asarray(G[key], np.float64) - ref) / np.maximum(np.abs(ref), 1e-3 * max(np.abs(ref).max(), 1e-30))
+        st[key] = (float(e.max()), float(np.quantile(e, 0.99)), _rel(G[key], ref))
+    print("per-element relative error (max, p99, per-tensor)", label, st)
+    REPORT.append(("grad", label, st))
+    return st
+
+
 def _gpu_grads(dv, grad_out):
     out, saved = T.raymarch_fwd(dv.ctx, dv.prims, dv.bvh, dv.rs, want_saved=True)
     g = torch.from_numpy(np.ascontiguousarray(grad_out, np.float32)).to(DEV)
@@ -49,6 +64,7 @@ def test_backward_matches_oracle_adjoint(seed, eps, bg):
     ref_out = oracle.render(sc, rays, F32M)
     if eps == 0.0:
         assert (ref_out["i_clamp"] >= 0).sum() > 10  # the clamped-sample branch is exercised
+        _per_element(G, R, f"small diff seed {seed} bg {bg}")
         for key in G:
             assert _rel(G[key], R[key]) <= 1e-3, (key, _rel(G[key], R[key]))
     else:
@@ -168,6 +184,7 @@ def test_backward_full_size_sampled_rays():
     _, G = _gpu_grads(dv, g)
     sub = rays_from(rays.o[sel], rays.d[sel], rays.t_near, rays.t_far, rays.dt)
     R = oracle.backward(sc, sub, g[sel].astype(np.float32).astype(np.float64), F32M)
+    _per_element(G, R, "full differentiation workload, 1500 rays")
     for key in G:
         assert _rel(G[key], R[key]) <= 1e-3, (key, _rel(G[key], R[key]))
 
