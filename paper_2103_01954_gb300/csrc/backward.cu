@@ -83,8 +83,8 @@ __device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs
       const int k = sh.ek[e];
       const Xform X = sh.exf[e];
       const void *pbase = sh.eptr[e];
-      const uint32_t rg = sh.erng[e][lane];
-      const int lo = (int)(rg & 0xffffu), hi = (int)(rg >> 16);
+      int lo, hi;
+      lane_range(sh, e, lane, lo, hi);
       const float4 tk = __ldg(reinterpret_cast<const float4 *>(a.pose + k) + 2);  // {R22, t0, t1, t2}
       const int rk = SEQ ? __ldg(a.rank + k) : 0;  // this primitive's leaf rank
       float2 acc[6];  // the 12 pose accumulators as packed pairs

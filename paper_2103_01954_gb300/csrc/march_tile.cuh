@@ -141,8 +141,9 @@ __device__ __forceinline__ void blend_sequential(const TileShared<CAP> &sh, int 
   float wlast = 0.0f;
   for (int p = 0; p < ne && rem > 0.0f; ++p) {
     const int e = sh.cand[p];
-    const uint32_t r = sh.erng[e][lane];
-    if ((int)(r & 0xffffu) > ii || (int)(r >> 16) < ii) continue;
+    int rlo, rhi;
+    lane_range(sh, e, lane, rlo, rhi);
+    if (rlo > ii || rhi < ii) continue;
     const float4 v = sample_rgba<DT, MT>(sh.exf[e], sh.eptr[e], x, M, Mm1, a.status);
     float w = v.w * a.dt;
     if (w >= rem) {  // this primitive's weight is clamped to what is left
@@ -296,8 +297,10 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
         int e;
         if (b0) { e = __ffs(b0) - 1; b0 &= b0 - 1; }
         else { e = 32 + __ffs(b1) - 1; b1 &= b1 - 1; }
-        const uint32_t rg = sh.erng[e][lane];
-        const int lo = max((int)(rg & 0xffffu), i), hi = min((int)(rg >> 16), ie - 1);
+        int lo, hi;
+        lane_range(sh, e, lane, lo, hi);
+        lo = max(lo, i);
+        hi = min(hi, ie - 1);
         if (!alive || lo > hi) continue;
         const Xform X = sh.exf[e];
         const char *pbase = sh.eptr[e];

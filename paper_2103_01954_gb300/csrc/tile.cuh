@@ -18,8 +18,12 @@ namespace mvp {
 constexpr int TILE_WARPS = 4;  // warps per block; a block covers 16x8 pixels
 constexpr int STACK = 256;     // traversal stack entries per warp
 constexpr int CBUF = 64;       // candidate leaves buffered per warp
-constexpr uint32_t EMPTY_RANGE = 0x0000ffffu;  // i_lo = 65535 > i_hi = 0
-constexpr int WINDOW_FULL = -1;   // build_window: more primitives than the list holds
+// A lane's sample range of a window entry, 8 + 8 bits: offsets of i_lo and i_hi from
+// the entry's tile range start elo (an entry whose tile range spans more than
+// MAX_SPAN samples does not fit: the window is split instead).
+constexpr uint16_t EMPTY_RANGE = 0x00ffu;  // i_lo = elo + 255 > i_hi = elo
+constexpr int MAX_SPAN = 254;
+constexpr int WINDOW_FULL = -1;   // build_window: more primitives than the list holds (or a span over MAX_SPAN)
 constexpr int WINDOW_STACK = -2;  // build_window: traversal stack overflow
 
 struct TileGeom {
@@ -197,7 +201,7 @@ struct TileShared {
   const char *eptr[CAP];  // payload of the entry's primitive
   int ek[CAP];
   int elo[CAP], ehi[CAP];
-  uint32_t erng[CAP][32];
+  uint16_t erng[CAP][32];  // per lane: (i_lo - elo) | (i_hi - elo) << 8
   unsigned int clk;  // the frame kernel's tile start (clock), for its tile schedule
 };
 
@@ -208,6 +212,15 @@ struct LeafRange {
   const int2 *range;
   int r0, r1;
 };
+
+// A lane's inclusive sample range [lo, hi] of window entry e (lo > hi: none).
+template <class SH>
+__device__ __forceinline__ void lane_range(const SH &sh, int e, int lane, int &lo, int &hi) {
+  const int base = sh.elo[e];
+  const uint32_t r = sh.erng[e][lane];
+  lo = base + (int)(r & 0xffu);
+  hi = base + (int)(r >> 8);
+}
 
 // Traverse the BVH for the packet over [ta, tb]. Candidate leaves (primitive ids)
 // are passed to `emit(nc)` in batches of up to CBUF via sh.cand; emit returns false
@@ -297,8 +310,9 @@ __device__ __forceinline__ void load_lane_ray(LaneRay &L, const float *__restric
 // a sample of the window with index <= lane_last (the lane's last live sample). The
 // first `skip` such primitives (in the fixed traversal order) are passed over.
 // Returns the number of entries; WINDOW_FULL if more than CAP remain after the
-// skipped ones (the list then holds the first CAP of them, ready to use);
-// WINDOW_STACK if the traversal stack overflowed.
+// skipped ones (the list then holds the first CAP of them, ready to use) or if an
+// entry's tile range spans more than MAX_SPAN samples (a window of at most MAX_SPAN + 1
+// samples never does); WINDOW_STACK if the traversal stack overflowed.
 template <int CAP, bool RANGED = false>
 __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__restrict__ nodes,
                                             const Pose *__restrict__ pose, const Xform *__restrict__ xf,
@@ -355,7 +369,11 @@ __device__ __forceinline__ int build_window(TileShared<CAP> &sh, const Node *__r
       }
       const int lo_min = __reduce_min_sync(FULL, has ? ilo : 0x7fffffff);
       const int hi_max = __reduce_max_sync(FULL, has ? ihi : -1);
-      sh.erng[ne][lane] = has ? ((uint32_t)ilo | ((uint32_t)ihi << 16)) : EMPTY_RANGE;
+      if (hi_max - lo_min > MAX_SPAN) {  // the lanes' offsets would not fit 8 bits: split the window
+        full = true;
+        return false;
+      }
+      sh.erng[ne][lane] = has ? (uint16_t)((ilo - lo_min) | ((ihi - lo_min) << 8)) : EMPTY_RANGE;
       if (lane == 0) {
         sh.ek[ne] = k;
         sh.elo[ne] = lo_min;
