@@ -52,3 +52,7 @@ def pytest_terminal_summary(terminalreporter):
         if kind == "grad":
             w(f"adjoint vs oracle ({label}): per element max / p99 / per tensor: " +
               ", ".join(f"{k} {v[0]:.2g}/{v[1]:.2g}/{v[2]:.2g}" for k, v in st.items()))
+    prec = [(label, st) for kind, label, st in REPORT if kind == "precision"]
+    if prec:
+        w("payload precision vs FP64 oracle on the FP32 payload (max / p99.9 over channels): " +
+          "; ".join(f"{label} {st['max']:.2g} / {st['p999']:.2g}" for label, st in prec))
