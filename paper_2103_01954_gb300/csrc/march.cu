@@ -163,10 +163,10 @@ static cudaError_t launch_march_m(const MarchArgs &a, cudaStream_t st) {
     return a.M == 16 ? launch_march_t<DT, MARCH_CAP, false, 16, true>(a, st)
                      : launch_march_t<DT, MARCH_CAP, false, 0, true>(a, st);
   switch (a.M) {
-    case 8: return launch_march_t<DT, MARCH_CAP, COUNT, 8>(a, st);
-    case 16: return launch_march_t<DT, MARCH_CAP, COUNT, 16>(a, st);
-    case 32: return launch_march_t<DT, MARCH_CAP, COUNT, 32>(a, st);
-    default: return launch_march_t<DT, MARCH_CAP, COUNT, 0>(a, st);
+    case 8: return launch_march_t<DT, march_cap<8>(), COUNT, 8>(a, st);
+    case 16: return launch_march_t<DT, march_cap<16>(), COUNT, 16>(a, st);
+    case 32: return launch_march_t<DT, march_cap<32>(), COUNT, 32>(a, st);
+    default: return launch_march_t<DT, march_cap<0>(), COUNT, 0>(a, st);
   }
 }
 

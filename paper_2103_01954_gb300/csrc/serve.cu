@@ -32,7 +32,6 @@
 
 namespace mvp {
 
-constexpr int SERVE_CAP = MARCH_CAP;
 constexpr int SERVE_STREAMS = 8;  // requests that may run at once without queueing on a stream
 
 // Completion record of a slot (mapped host memory): written by the device.
@@ -79,7 +78,8 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, DT == MVP_F32 ? MVP_MARCH_MIN
     k_serve(const __grid_constant__ ServeReq R) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  TileShared<SERVE_CAP> &sh = reinterpret_cast<TileShared<SERVE_CAP> *>(smem_raw)[warp];
+  constexpr int CAP = march_cap<MT>();
+  TileShared<CAP> &sh = reinterpret_cast<TileShared<CAP> *>(smem_raw)[warp];
   const int64_t wt = (int64_t)blockIdx.x * TILE_WARPS + warp;
   const int64_t n_view = R.m.geom.n_warp_tiles;  // tiles per view
   const int64_t n_tiles = n_view * R.views;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, DT == MVP_F32 ? MVP_MARCH_MIN
 #pragma unroll
     for (int j = 0; j < 3; ++j) L.o[j] = L.d[j] = 0.0f;
   }
-  if (__ballot_sync(FULL, L.r >= 0) != 0) march_tile<DT, SERVE_CAP, false, MT>(sh, R.m, L);
+  if (__ballot_sync(FULL, L.r >= 0) != 0) march_tile<DT, CAP, false, MT>(sh, R.m, L);
   __syncwarp();
   if (lane == 0) {
     __threadfence();  // this tile's pixels are visible before it is counted
@@ -123,6 +123,15 @@ static const ServeKernel k_serve_table[SERVE_CLASSES] = {
     k_serve<MVP_F32, 8>,  k_serve<MVP_F32, 16>,  k_serve<MVP_F32, 32>,  k_serve<MVP_F32, 0>,
     k_serve<MVP_BF16, 8>, k_serve<MVP_BF16, 16>, k_serve<MVP_BF16, 32>, k_serve<MVP_BF16, 0>,
     k_serve<MVP_F16, 8>,  k_serve<MVP_F16, 16>,  k_serve<MVP_F16, 32>,  k_serve<MVP_F16, 0>};
+// dynamic shared memory of each class's kernel (its window capacity depends on M)
+inline size_t serve_smem(int cls) {
+  switch (cls & 3) {
+    case 0: return sizeof(TileShared<march_cap<8>()>) * TILE_WARPS;
+    case 1: return sizeof(TileShared<march_cap<16>()>) * TILE_WARPS;
+    case 2: return sizeof(TileShared<march_cap<32>()>) * TILE_WARPS;
+    default: return sizeof(TileShared<march_cap<0>()>) * TILE_WARPS;
+  }
+}
 
 }  // namespace mvp
 
@@ -275,7 +284,8 @@ mvp_status launch(mvp_server *S, InFlight &f) {
   }
   S->next_stream = (best + 1) % mvp::SERVE_STREAMS;
   const unsigned blocks = (unsigned)(m.geom.n_warp_tiles * R.views / mvp::TILE_WARPS);
-  mvp::k_serve_table[mvp::serve_class(m.dtype, m.M)]<<<blocks, mvp::TILE_WARPS * 32, S->smem, S->streams[best]>>>(R);
+  const int cls = mvp::serve_class(m.dtype, m.M);
+  mvp::k_serve_table[cls]<<<blocks, mvp::TILE_WARPS * 32, mvp::serve_smem(cls), S->streams[best]>>>(R);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return serve_fail(MVP_ERR_CUDA, cudaGetErrorString(e));
   f.stream = best;
@@ -386,12 +396,13 @@ mvp_status mvp_serve_create(mvp_ctx *ctx, size_t hbm_budget, int32_t max_slots, 
   for (cudaStream_t &st : S->streams)
     if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return bail("stream");
   if ((e = cudaStreamCreateWithFlags(&S->copy, cudaStreamNonBlocking)) != cudaSuccess) return bail("copy stream");
-  S->smem = sizeof(mvp::TileShared<mvp::SERVE_CAP>) * mvp::TILE_WARPS;
-  for (mvp::ServeKernel k : mvp::k_serve_table)
-    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem)) != cudaSuccess)
+  S->smem = mvp::serve_smem(1);  // the 16^3 class, for the grid size below
+  for (int c = 0; c < mvp::SERVE_CLASSES; ++c)
+    if ((e = cudaFuncSetAttribute(mvp::k_serve_table[c], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)mvp::serve_smem(c))) != cudaSuccess)
       return bail("kernel attribute");
   int per_sm = 0, sms = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mvp::k_serve_table[0], mvp::TILE_WARPS * 32, S->smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mvp::k_serve_table[1], mvp::TILE_WARPS * 32, S->smem);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   S->grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
   *out = S;
