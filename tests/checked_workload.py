@@ -20,11 +20,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-def _stack(n, seed):
+def _stack(n, seed, M=3):
     import synthetic
 
     rng = np.random.default_rng(seed)
-    M = 3
     payload = np.zeros((n, M, M, M, 4), np.float32)
     payload[..., :3] = rng.uniform(0.0, 1.0, (n, 1, 1, 1, 3)).astype(np.float32)
     payload[..., 3] = 0.004 * rng.uniform(0.5, 1.5, (n, M, M, M)).astype(np.float32)
@@ -101,6 +100,7 @@ def run() -> dict:
     cam = synthetic.look_at_camera((0.3, -0.2, -3.0), 20, 12, 16.0)
     rays = synthetic.make_rays([cam], 1.0, 5.0, 0.02)
     frame("stack150", _stack(150, 3), rays, grads=True)  # window splitting and the overflow path
+    frame("stack150_m8", _stack(150, 4, M=8), rays)  # the same with 64-entry windows (8^3 payloads)
     # the adjoint replayed primitive group by primitive group (mask, work list, persistent replay)
     ctx.set_bwd_group_bytes(1)
     frame("stack150_grouped", _stack(150, 3), rays, grads=True)

@@ -69,26 +69,27 @@ def test_sequential_vs_definition(cfg):
     definition_bar(out.cpu().numpy(), oracle.render(sc, rays, F64M | oracle.SEQUENTIAL), "sequential " + cfg)
 
 
-def _stack_scene(n, seed):
+def _stack_scene(n, seed, M=3):
     rng = np.random.default_rng(seed)
-    base = single_box(M=3, alpha=0.004, s=(0.5, 0.5, 0.5))
+    base = single_box(M=M, alpha=0.004, s=(0.5, 0.5, 0.5))
     payload = np.repeat(base.payload, n, 0)
     payload[..., :3] = rng.uniform(0.0, 1.0, (n, 1, 1, 1, 3)).astype(np.float32)
-    payload[..., 3] *= rng.uniform(0.5, 1.5, (n, 3, 3, 3)).astype(np.float32)
+    payload[..., 3] *= rng.uniform(0.5, 1.5, (n, M, M, M)).astype(np.float32)
     t = rng.uniform(-0.05, 0.05, (n, 3)).astype(np.float32)
     return synthetic.Scene(t=t, q=synthetic.random_unit_quaternions(rng, n), s=np.repeat(base.s, n, 0),
-                           payload=payload, M=3)
+                           payload=payload, M=M)
 
 
-@pytest.mark.parametrize("n", [49, 150])
-def test_overlap_beyond_a_window_vs_definition(n):
-    """More primitives at one sample than a tile's window list holds (48)."""
-    sc = _stack_scene(n, n)
+@pytest.mark.parametrize("n,M", [(49, 3), (150, 3), (65, 8), (150, 8)])
+def test_overlap_beyond_a_window_vs_definition(n, M):
+    """More primitives at one sample than a tile's window list holds (48 entries; 64 for
+    8^3 payloads)."""
+    sc = _stack_scene(n, n, M)
     cam = synthetic.look_at_camera((0.3, -0.2, -3.0), 20, 12, 16.0)
     rays = synthetic.make_rays([cam], 1.0, 5.0, 0.02)
     out, _ = Dev(sc, rays).build().render()
     ref = oracle.render(sc, rays, F64M)
-    definition_bar(out.cpu().numpy(), ref, f"stack{n}")
+    definition_bar(out.cpu().numpy(), ref, f"stack{n} M{M}")
     assert ref["n_eval"].max() >= n
 
 
