@@ -205,7 +205,9 @@ MVP_API mvp_status mvp_ctx_set_tile_schedule(mvp_ctx *ctx, int32_t enable);
  * per group its rays meet, group after group, so that a group's payload and
  * g_payload stay in L2 while all rays that touch them are replayed. bytes = 0 picks
  * the size from the device's L2 (a third of it; the default); bytes < 0 never
- * groups. Results equal the ungrouped replay up to the order of the float
+ * groups. The grouped replay takes stream-ordered scratch (cudaMallocAsync, about
+ * 8 + 4 x groups bytes per warp tile); where that allocation fails the call replays in
+ * one pass. Results equal the ungrouped replay up to the order of the float
  * reductions. */
 MVP_API mvp_status mvp_ctx_set_bwd_group_bytes(mvp_ctx *ctx, int64_t bytes);
 /* Render: out_rgba [n][4] float32 device = (I + (1 - A) bg, A). `saved`

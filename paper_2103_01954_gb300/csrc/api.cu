@@ -512,17 +512,22 @@ mvp_status mvp_raymarch_bwd(mvp_ctx *ctx, const mvp_prims *prims, mvp_bvh *bvh, 
     budget = l2 > 0 ? l2 / 3 : 0;
   }
   const int n = prims->n;
-  if (budget > 0 && n > 1 && per_prim * n > 2 * budget && b.m.geom.n_warp_tiles <= 0x7fffffff / 64) {
-    mvp::BwdGroups gr;
+  mvp::BwdGroups gr;
+  char *scratch = nullptr;
+  const int64_t nt = b.m.geom.n_warp_tiles;
+  if (budget > 0 && n > 1 && per_prim * n > 2 * budget && nt <= 0x7fffffff / 64) {
     gr.gsize = (int)std::max<int64_t>(1, std::min<int64_t>(n, budget / per_prim));
     if ((n + gr.gsize - 1) / gr.gsize > 64) gr.gsize = (n + 63) / 64;
     gr.n_groups = (n + gr.gsize - 1) / gr.gsize;
     gr.range = reinterpret_cast<const int2 *>(bvh->b.parent);
     // stream-ordered scratch: mask, work list, group offsets, work counter
-    const int64_t nt = b.m.geom.n_warp_tiles;
     const size_t bytes = (size_t)nt * 8 + (size_t)nt * gr.n_groups * 4 + (size_t)(gr.n_groups + 2) * 4;
-    char *scratch = nullptr;
-    if ((e = cudaMallocAsync(&scratch, bytes, st)) != cudaSuccess) return cuda_fail(e, "adjoint group scratch");
+    if (cudaMallocAsync(&scratch, bytes, st) != cudaSuccess) {
+      cudaGetLastError();  // no room for the work list: replay in one pass below (same gradients)
+      scratch = nullptr;
+    }
+  }
+  if (scratch) {
     gr.mask = reinterpret_cast<unsigned long long *>(scratch);
     gr.items = reinterpret_cast<int *>(scratch + (size_t)nt * 8);
     gr.goff = gr.items + (size_t)nt * gr.n_groups;
