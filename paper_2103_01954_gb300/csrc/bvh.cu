@@ -561,15 +561,29 @@ __device__ __forceinline__ void write_internal(Node *__restrict__ nodes, int i, 
 // (range[i]). Blocks of 1024 also union their leaves'
 // boxes in chunks of 32 (chunk1, one per warp) and 1024 (chunk2, one per block) for
 // the range refit.
+// STAGED (n <= HIER_STAGE_N): every block first copies the sorted keys into shared
+// memory, so the searches of the hierarchy read shared memory instead of L2.
 constexpr int HIER_THREADS = 1024;
+constexpr int HIER_STAGE_N = 8192;  // keys staged per block: 8 bytes each, 64 KB at most
+template <bool STAGED>
 __global__ void __launch_bounds__(HIER_THREADS) k_hierarchy(const uint32_t *__restrict__ km,
                                                             const int *__restrict__ kv, int n,
                                                             const float4 *__restrict__ pbox, Node *__restrict__ nodes,
                                                             int2 *__restrict__ range, float4 *__restrict__ chunk1,
                                                             float4 *__restrict__ chunk2, int *__restrict__ rank) {
   __shared__ float sc[32][6];
+  extern __shared__ __align__(16) unsigned char hier_smem[];
+  uint32_t *skm = reinterpret_cast<uint32_t *>(hier_smem);
+  int *skv = reinterpret_cast<int *>(hier_smem + sizeof(uint32_t) * (STAGED ? n : 0));
   pdl_wait();
   pdl_trigger();
+  if (STAGED) {
+    for (int a = threadIdx.x; a < n; a += HIER_THREADS) {
+      skm[a] = km[a];
+      skv[a] = kv[a];
+    }
+    __syncthreads();
+  }
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i = blockIdx.x * HIER_THREADS + tid;
   float b[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
@@ -607,7 +621,9 @@ __global__ void __launch_bounds__(HIER_THREADS) k_hierarchy(const uint32_t *__re
     }
   }
   if (i >= n - 1) return;
-  auto key = [&](int a) -> uint64_t { return ((uint64_t)km[a] << 32) | (uint32_t)kv[a]; };
+  auto key = [&](int a) -> uint64_t {
+    return STAGED ? ((uint64_t)skm[a] << 32) | (uint32_t)skv[a] : ((uint64_t)km[a] << 32) | (uint32_t)kv[a];
+  };
   int lc, rc, j;
   internal_children(key, n, i, lc, rc, j);
   write_internal(nodes, i, lc, rc);
@@ -768,9 +784,16 @@ cudaError_t bvh_build(BvhBuffers &b, const float *t, const float *q, const float
   // second key and value buffers (n/32 and n/1024 boxes of 32 bytes fit in 4n bytes)
   int2 *range = reinterpret_cast<int2 *>(b.parent);
   float4 *chunk1 = reinterpret_cast<float4 *>(b.keys_b), *chunk2 = reinterpret_cast<float4 *>(b.vals_b);
-  cudaError_t e = pdl_launch(k_hierarchy, dim3((n + HIER_THREADS - 1) / HIER_THREADS), dim3(HIER_THREADS), 0, st,
-                             (const uint32_t *)b.keys_a, (const int *)b.vals_a, n, (const float4 *)b.pbox, b.nodes,
-                             range, chunk1, chunk2, b.rank);
+  const bool staged = n <= HIER_STAGE_N;
+  const size_t hsmem = staged ? (size_t)n * 8 : 0;
+  cudaError_t e = staged ? allow_dynamic_smem(reinterpret_cast<const void *>(k_hierarchy<true>), hsmem) : cudaSuccess;
+  if (e == cudaSuccess)
+    e = staged ? pdl_launch(k_hierarchy<true>, dim3((n + HIER_THREADS - 1) / HIER_THREADS), dim3(HIER_THREADS), hsmem,
+                            st, (const uint32_t *)b.keys_a, (const int *)b.vals_a, n, (const float4 *)b.pbox, b.nodes,
+                            range, chunk1, chunk2, b.rank)
+               : pdl_launch(k_hierarchy<false>, dim3((n + HIER_THREADS - 1) / HIER_THREADS), dim3(HIER_THREADS), 0, st,
+                            (const uint32_t *)b.keys_a, (const int *)b.vals_a, n, (const float4 *)b.pbox, b.nodes,
+                            range, chunk1, chunk2, b.rank);
   if (e == cudaSuccess && n > 1)
     e = pdl_launch(k_refit_ranges, dim3((n - 1 + REFIT_WARPS - 1) / REFIT_WARPS), dim3(REFIT_WARPS * 32), 0, st,
                    b.nodes, (const int2 *)range, (const float4 *)chunk1, (const float4 *)chunk2, n);
