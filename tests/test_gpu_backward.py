@@ -235,3 +235,23 @@ def test_grouped_adjoint_equals_ungrouped(cfg, dtype, sequential, budget):
     if dtype == torch.float32 and not sequential:
         R = oracle.backward(sc, rays, g.astype(np.float32).astype(np.float64), F32M)
         assert _rel(grouped["g_payload"], R["g_payload"]) <= 1e-3
+
+
+def test_grouped_adjoint_on_one_dimensional_rays_with_a_ragged_tail():
+    """Rays given as a flat list (32-ray tiles, not image tiles) whose count leaves a partly
+    empty last tile: the group masks, work list and replay against the one-pass replay."""
+    sc, img_rays, _ = synthetic.make_config("diff_small_64x8^3_2x48x40", 4)
+    sel = np.random.default_rng(5).choice(img_rays.n, 3001, replace=False)
+    rays = rays_from(img_rays.o[sel], img_rays.d[sel], img_rays.t_near, img_rays.t_far, img_rays.dt)
+    dv = Dev(sc, rays).build()
+    g = np.random.default_rng(6).standard_normal((rays.n, 4))
+    dv.ctx.set_bwd_group_bytes(-1)
+    _, plain = _gpu_grads(dv, g)
+    dv.ctx.set_bwd_group_bytes(20_000)
+    _, grouped = _gpu_grads(dv, g)
+    for key in plain:
+        err = np.abs(grouped[key].astype(np.float64) - plain[key]).max() / max(np.abs(plain[key]).max(), 1e-30)
+        assert err <= 1e-5, (key, err)
+    R = oracle.backward(sc, rays, g.astype(np.float32).astype(np.float64), F32M)
+    for key in grouped:
+        assert _rel(grouped[key], R[key]) <= 1e-3, key
