@@ -30,6 +30,10 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "paper_4096x16^3_667x1024"
 METRIC = "MVP raymarch Mrays/s fwd & fwd+bwd vs plain FP32; serving p50/p99 ms/frame"
+# resident 4-warp blocks per SM of the march and adjoint kernels (their launch bounds;
+# registers allow no more): the residency the gather probe is also run at
+MARCH_BLOCKS_PER_SM = 5
+ADJOINT_BLOCKS_PER_SM = 3
 
 # Algorithmic work per (sample, primitive) evaluation: 8 voxel reads of 4 channels
 # (bytes by dtype) and the FP32 operations of the definition (local coordinates
@@ -818,7 +822,18 @@ def _gather_probe(torch, T):
     g = torch.zeros((n32, M, M, M, 4), dtype=torch.float32, device=dev)
     acc, ms = timed(None, B.MVP_F32, n32, 1, 1, grad=g)
     out["scatter_f32x4_l2_Gupdates_s"] = round(acc / (ms * 1e-3) / 1e9, 2)
+    # the same accesses at the residency the kernels get (4-warp blocks holding the march's
+    # shared memory: 5 per SM for the march, 3 for the adjoint, as their launch bounds give)
+    acc, ms = timed(None, B.MVP_F32, n32, 1 | (ADJOINT_BLOCKS_PER_SM << 8), 1, grad=g)
+    out["scatter_f32x4_l2_at_adjoint_residency_Gupdates_s"] = round(acc / (ms * 1e-3) / 1e9, 2)
     del g
+    for name, tdt, dtype, vb in (("f32", torch.float32, B.MVP_F32, 16), ("bf16", torch.bfloat16, B.MVP_BF16, 8)):
+        n = n32 * 16 // vb
+        payload = torch.rand((n, M, M, M, 4), device=dev).to(tdt)
+        for fp, tag in ((0, "l1"), (1, "l2")):
+            acc, ms = timed(payload, dtype, n, 0 | (MARCH_BLOCKS_PER_SM << 8), fp)
+            out[f"gather_{name}_{tag}_at_march_residency_GBps"] = round(acc * vb / (ms * 1e-3) / 1e9, 1)
+        del payload
     torch.cuda.empty_cache()
     return out
 
@@ -842,6 +857,9 @@ def _summary(variants, serving, probe):
     for k in ("bf16_over_f32", "e2e_bf16_over_f32"):
         if k in variants:
             out[k] = variants[k]
+    if isinstance(variants.get("fwd_bwd_f32_512x32^3_4x512x512"), dict):
+        out["backward_scatter_frac_at_kernel_residency"] = \
+            variants["fwd_bwd_f32_512x32^3_4x512x512"]["backward_roofline"]["frac_at_kernel_residency"]
     if isinstance(variants.get("fwd_bf16"), dict) and "gather_frac" in variants["fwd_bf16"]:
         out["fwd_bf16_gather_frac"] = variants["fwd_bf16"]["gather_frac"]
     for k, v in probe.items():
@@ -907,6 +925,9 @@ def run_gpu(args):
                 "peak_kind": "measured: mvp_gather_probe, the march's 8-corner FP32 gathers, L1-resident",
                 "peak_l2_resident_GBps": probe["gather_f32_l2_GBps"],
                 "frac_of_l2_resident": round(gather / probe["gather_f32_l2_GBps"], 4),
+                "peak_at_kernel_residency_GBps": probe["gather_f32_l1_at_march_residency_GBps"],
+                "frac_at_kernel_residency": round(gather / probe["gather_f32_l1_at_march_residency_GBps"], 4),
+                "residency_note": "the same gathers at the march's 5 blocks of 4 warps per SM and its L1 size",
                 "kernel": "k_march<f32>", "march_ms": round(march_ms, 4), "evaluations": n_eval,
                 "bytes_per_evaluation": GATHER_BYTES["f32"],
                 "l1_wavefront_frac": ncu.get("l1_wavefront_frac"),
@@ -990,6 +1011,10 @@ def run_gpu(args):
                                   "peak_Gupdates_s": probe["scatter_f32x4_l2_Gupdates_s"],
                                   "peak_kind": "measured: mvp_gather_probe mode 1, L2-resident footprint",
                                   "frac": round(upd / probe["scatter_f32x4_l2_Gupdates_s"], 4),
+                                  "peak_at_kernel_residency_Gupdates_s":
+                                      probe["scatter_f32x4_l2_at_adjoint_residency_Gupdates_s"],
+                                  "frac_at_kernel_residency":
+                                      round(upd / probe["scatter_f32x4_l2_at_adjoint_residency_Gupdates_s"], 4),
                                   "algorithmic_bytes": alg,
                                   "traffic": nb.get("dram_bytes_per_launch"),
                                   "traffic_over_algorithmic": (round(nb["dram_bytes_per_launch"] / alg, 3)

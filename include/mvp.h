@@ -390,6 +390,11 @@ MVP_API mvp_status mvp_volume_prior(mvp_ctx *ctx, const float *s, int32_t n, flo
  * meaningless). *accesses (host, nullable) = voxel accesses of the launch (each 16 B
  * FP32 or 8 B BF16/FP16). Arrays are device memory owned by the caller: payload 16-byte
  * (FP32) or 8-byte aligned (times 2 in mode 2 and 4 in mode 3), grad 16-byte aligned.
+ * mode | (B << 8), B in 1..16, for modes 0 and 1: the same accesses at a fixed residency
+ * of B 4-warp blocks per SM, each holding the march kernels' shared memory, under a
+ * carveout that fits exactly B of them (the march runs 5 such blocks per SM, the adjoint
+ * 3): the ceiling at the warps and L1 those kernels actually get; MVP_ERR_INVALID_ARG if
+ * the device does not give that residency.
  * MVP_ERR_INVALID_ARG for bad sizes, modes or alignment. Asynchronous on `stream`; time it with events on that stream. */
 MVP_API mvp_status mvp_gather_probe(const void *payload, int32_t dtype, int32_t n, int32_t M, int32_t mode,
                                     int32_t footprint, int32_t steps, float *grad, float *sink, int64_t *accesses,

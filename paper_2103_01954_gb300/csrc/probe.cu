@@ -113,11 +113,13 @@ __device__ __forceinline__ int cell(float base, float step, float lane_off, int 
   return c < 0 ? 0 : (c > M - 2 ? M - 2 : c);
 }
 
-template <int DT, bool SCATTER, int PER = 1>
+// RES: launched at a fixed residency (128-thread blocks, see mvp_gather_probe); a
+// separate instance, so its shared-memory carveout leaves the full-occupancy one alone.
+template <int DT, bool SCATTER, int PER = 1, bool RES = false>
 __global__ void __launch_bounds__(PROBE_THREADS) k_probe(const void *payload, float4 *grad, int n, int M,
                                                          int footprint, int steps, float *sink) {
   const int lane = threadIdx.x & 31;
-  const uint32_t warp = (blockIdx.x * PROBE_THREADS + threadIdx.x) >> 5;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const float lx = 0.25f * (float)(lane & 7), ly = 0.25f * (float)(lane >> 3);
   const int64_t M3 = (int64_t)M * M * M;
   const int64_t o1 = 1, oM = M, oM2 = (int64_t)M * M;
@@ -299,6 +301,29 @@ cudaError_t launch_staged(const void *payload, int n, int M, int footprint, int 
   return cudaGetLastError();
 }
 
+// The kernels of the frame march and the adjoint run 4-warp blocks holding
+// sizeof(TileShared<MARCH_CAP>) x 4 bytes of shared memory each, `blocks` of them per SM
+// (registers allow no more). This launches the probe the same way: 128-thread blocks
+// with that much dynamic shared memory and a carveout that holds exactly `blocks` of
+// them, so the probe sees the same warps per SM and the same L1 size. Returns
+// cudaErrorInvalidConfiguration if the device does not give that residency.
+template <int DT, bool SCATTER>
+cudaError_t launch_resident(const void *payload, float4 *grad, int n, int M, int footprint, int steps, float *sink,
+                            int blocks, int sms, int smem_per_sm, cudaStream_t st) {
+  auto k = k_probe<DT, SCATTER, 1, true>;
+  const size_t smem = sizeof(TileShared<MARCH_CAP>) * TILE_WARPS;
+  const int need = (int)(blocks * (smem + 1024));  // 1 KB per block is the driver's
+  const int pct = (need * 100 + smem_per_sm - 1) / smem_per_sm;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct > 100 ? 100 : pct);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128, smem)) != cudaSuccess) return e;
+  if (per_sm != blocks) return cudaErrorInvalidConfiguration;
+  k<<<sms * blocks, 128, smem, st>>>(payload, grad, n, M, footprint, steps, sink);
+  return cudaGetLastError();
+}
+
 template <int PER>
 cudaError_t launch_loads(int dtype, const void *payload, int n, int M, int footprint, int steps, float *sink,
                          int grid, cudaStream_t st) {
@@ -314,8 +339,13 @@ extern "C" mvp_status mvp_gather_probe(const void *payload, int32_t dtype, int32
                                        int32_t footprint, int32_t steps, float *grad, float *sink, int64_t *accesses,
                                        mvp_stream stream) {
   using namespace mvp;
-  if (n < 1 || M < 2 || M > MVP_MAX_M || steps < 1 || mode < 0 || mode > 4 || (footprint != 0 && footprint != 1))
+  // bits 0-7: the access mode; bits 8-15: 4-warp blocks per SM (0: every SM full)
+  const int blocks = (mode >> 8) & 0xff;
+  const bool bad_mode = mode < 0 || (mode >> 16) != 0 || (mode & 0xff) > 4 || blocks > 16 ||
+                        (blocks > 0 && (mode & 0xff) > 1);
+  if (n < 1 || M < 2 || M > MVP_MAX_M || steps < 1 || bad_mode || (footprint != 0 && footprint != 1))
     return record_error("mvp_gather_probe: bad n, M, steps, mode or footprint"), MVP_ERR_INVALID_ARG;
+  mode &= 0xff;
   if (mode != 1 && (!payload || !sink || (dtype != MVP_F32 && dtype != MVP_BF16 && dtype != MVP_F16)))
     return record_error("mvp_gather_probe: loads need a payload, a sink and a payload dtype"), MVP_ERR_INVALID_ARG;
   if (mode == 1 && !grad) return record_error("mvp_gather_probe: reductions need grad"), MVP_ERR_INVALID_ARG;
@@ -334,6 +364,23 @@ extern "C" mvp_status mvp_gather_probe(const void *payload, int32_t dtype, int32
   cudaStream_t st = (cudaStream_t)stream;
   float4 *g4 = reinterpret_cast<float4 *>(grad);
   cudaError_t e;
+  if (blocks > 0) {
+    int smem_per_sm = 0;
+    if (cudaDeviceGetAttribute(&smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        smem_per_sm <= 0)
+      return record_error("mvp_gather_probe: no device"), MVP_ERR_CUDA;
+    if (mode == 1) e = launch_resident<MVP_F32, true>(nullptr, g4, n, M, footprint, steps, nullptr, blocks, sms, smem_per_sm, st);
+    else if (dtype == MVP_F32) e = launch_resident<MVP_F32, false>(payload, nullptr, n, M, footprint, steps, sink, blocks, sms, smem_per_sm, st);
+    else if (dtype == MVP_BF16) e = launch_resident<MVP_BF16, false>(payload, nullptr, n, M, footprint, steps, sink, blocks, sms, smem_per_sm, st);
+    else e = launch_resident<MVP_F16, false>(payload, nullptr, n, M, footprint, steps, sink, blocks, sms, smem_per_sm, st);
+    if (e == cudaErrorInvalidConfiguration) {
+      cudaGetLastError();
+      return record_error("mvp_gather_probe: the device does not give that residency"), MVP_ERR_INVALID_ARG;
+    }
+    if (e != cudaSuccess) return record_error("mvp_gather_probe: launch failed"), MVP_ERR_CUDA;
+    if (accesses) *accesses = (int64_t)sms * blocks * 128 * steps * 8;
+    return MVP_OK;
+  }
   if (mode == 1) e = launch_probe_t<MVP_F32, true, 1>(nullptr, g4, n, M, footprint, steps, nullptr, grid, st);
   else if (mode == 0) e = launch_loads<1>(dtype, payload, n, M, footprint, steps, sink, grid, st);
   else if (mode == 2) e = launch_loads<2>(dtype, payload, n, M, footprint, steps, sink, grid, st);

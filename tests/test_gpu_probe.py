@@ -56,12 +56,36 @@ def test_probe_reduces_every_access(M):
     assert grad.abs().sum().item() > 0
 
 
+@pytest.mark.parametrize("blocks", [3, 5])
+@pytest.mark.parametrize("footprint", [0, 1])
+def test_probe_at_the_kernels_residency_counts_every_access(blocks, footprint):
+    """mode | (blocks << 8): 4-warp blocks at the march kernels' residency; loads and
+    reductions are still all performed, and the access count is that launch's."""
+    n, M = 200, 16
+    payload = torch.ones((n, M, M, M, 4), dtype=torch.float32, device=DEV)
+    sink = torch.zeros(1, dtype=torch.float32, device=DEV)
+    st, acc = _probe(payload, B.MVP_F32, n, M, 0 | (blocks << 8), footprint, 8, sink=sink)
+    B.check(st, "probe at residency")
+    torch.cuda.synchronize()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert acc == sms * blocks * 128 * 8 * 8
+    assert sink.item() == 4.0 * acc
+    grad = torch.zeros((64, M, M, M, 4), dtype=torch.float32, device=DEV)
+    st, acc = _probe(None, B.MVP_F32, 64, M, 1 | (blocks << 8), footprint, 4, grad=grad)
+    B.check(st, "reductions at residency")
+    torch.cuda.synchronize()
+    assert abs(grad.double().sum().item() - acc * 0.010) <= 1e-4 * acc * 0.010
+
+
 def test_probe_rejects_bad_arguments():
     sink = torch.zeros(1, dtype=torch.float32, device=DEV)
     p = torch.ones((4, 8, 8, 8, 4), dtype=torch.float32, device=DEV)
     assert _probe(p, B.MVP_F32, 0, 8, 0, 0, 4, sink=sink)[0] == B.MVP_ERR_INVALID_ARG
     assert _probe(p, B.MVP_F32, 4, 1, 0, 0, 4, sink=sink)[0] == B.MVP_ERR_INVALID_ARG
     assert _probe(p, B.MVP_F32, 4, 8, 5, 0, 4, sink=sink)[0] == B.MVP_ERR_INVALID_ARG
+    assert _probe(p, B.MVP_F32, 4, 8, 2 | (5 << 8), 0, 4, sink=sink)[0] == B.MVP_ERR_INVALID_ARG  # layouts: full only
+    assert _probe(p, B.MVP_F32, 4, 8, 0 | (17 << 8), 0, 4, sink=sink)[0] == B.MVP_ERR_INVALID_ARG
+    assert _probe(p, B.MVP_F32, 4, 8, 1 << 16, 0, 4, sink=sink)[0] == B.MVP_ERR_INVALID_ARG
     assert _probe(p, B.MVP_F32, 4, 8, 0, 0, 4)[0] == B.MVP_ERR_INVALID_ARG  # no sink
     assert _probe(None, B.MVP_F32, 4, 8, 1, 0, 4)[0] == B.MVP_ERR_INVALID_ARG  # no grad
     v = p.view(-1)[1:]  # 4-byte offset: misaligned for 16-byte voxels
