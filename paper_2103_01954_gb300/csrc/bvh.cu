@@ -620,6 +620,11 @@ __global__ void __launch_bounds__(HIER_THREADS) k_hierarchy(const uint32_t *__re
       chunk2[2 * blockIdx.x + 1] = make_float4(c[3], c[4], c[5], 0.0f);
     }
   }
+  if (i == 0) {  // the traversal's starting cut until the refit widens it: the root alone
+    int *cut = reinterpret_cast<int *>(nodes + 2 * n - 1);
+    cut[0] = 1;
+    cut[1] = 0;
+  }
   if (i >= n - 1) return;
   auto key = [&](int a) -> uint64_t {
     return STAGED ? ((uint64_t)skm[a] << 32) | (uint32_t)skv[a] : ((uint64_t)km[a] << 32) | (uint32_t)kv[a];
@@ -637,6 +642,45 @@ __global__ void __launch_bounds__(HIER_THREADS) k_hierarchy(const uint32_t *__re
 // single leaves at its ends, a few coalesced loads per lane. No node waits for
 // another.
 constexpr int REFIT_WARPS = 8;
+
+// The traversal's starting cut (one warp): the tree expanded level by level from the root
+// while the nodes still fit 32, so a traversal tests the top levels in one step instead
+// of one step per level. Written as {count, nodes...} (nodes cover every leaf once).
+__device__ void build_cut(const Node *__restrict__ nodes, int n, int *buf, int *cut) {
+  const int lane = threadIdx.x & 31;
+  int node = lane == 0 ? 0 : -1;
+  int cnt = 1;
+  while (true) {
+    const bool inner = node >= 0 && node < n - 1;
+    const int ni = __popc(__ballot_sync(FULL, inner));
+    if (ni == 0 || cnt + ni > 32) break;
+    int l = -1, r = -1;
+    if (inner) {
+      l = nodes[node].left;
+      r = nodes[node].right;
+    }
+    const int k = node < 0 ? 0 : (inner ? 2 : 1);  // entries this lane's node becomes
+    int pre = k;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(FULL, pre, o);
+      if (lane >= o) pre += v;
+    }
+    pre -= k;
+    if (k == 1) buf[pre] = node;
+    if (k == 2) {
+      buf[pre] = l;
+      buf[pre + 1] = r;
+    }
+    __syncwarp();
+    cnt += ni;
+    node = lane < cnt ? buf[lane] : -1;
+    __syncwarp();
+  }
+  if (lane == 0) cut[0] = cnt;
+  if (lane < cnt) cut[1 + lane] = node;
+}
+
 __global__ void __launch_bounds__(REFIT_WARPS * 32) k_refit_ranges(Node *__restrict__ nodes,
                                                                    const int2 *__restrict__ range,
                                                                    const float4 *__restrict__ chunk1,
@@ -644,6 +688,11 @@ __global__ void __launch_bounds__(REFIT_WARPS * 32) k_refit_ranges(Node *__restr
   pdl_wait();
   pdl_trigger();  // the march may be scheduled now; it waits for this grid
   const int lane = threadIdx.x & 31;
+  if (blockIdx.x == gridDim.x - 1) {  // the extra block: the traversal's starting cut
+    __shared__ int buf[32];
+    if (threadIdx.x < 32) build_cut(nodes, n, buf, reinterpret_cast<int *>(nodes + 2 * n - 1));
+    return;
+  }
   const int i = blockIdx.x * REFIT_WARPS + (threadIdx.x >> 5);
   if (i >= n - 1) return;
   const int2 r = range[i];
@@ -715,7 +764,7 @@ cudaError_t bvh_reserve(BvhBuffers &b, int n) {
   size_t o_va = off; off = align_up(off + (size_t)cap * sizeof(int));
   size_t o_vb = off; off = align_up(off + (size_t)cap * sizeof(int));
   size_t o_cnt = off; off = align_up(off + (size_t)256 * G * sizeof(int));
-  size_t o_nodes = off; off = align_up(off + (size_t)(2 * cap) * sizeof(Node));
+  size_t o_nodes = off; off = align_up(off + (size_t)(2 * cap + CUT_NODES) * sizeof(Node));
   size_t o_par = off; off = align_up(off + (size_t)(2 * cap) * sizeof(int));
   size_t o_gmc = off; off = align_up(off + (size_t)cap * 12 * sizeof(float));
   size_t o_rank = off; off = align_up(off + (size_t)cap * sizeof(int));
@@ -795,7 +844,7 @@ cudaError_t bvh_build(BvhBuffers &b, const float *t, const float *q, const float
                             (const uint32_t *)b.keys_a, (const int *)b.vals_a, n, (const float4 *)b.pbox, b.nodes,
                             range, chunk1, chunk2, b.rank);
   if (e == cudaSuccess && n > 1)
-    e = pdl_launch(k_refit_ranges, dim3((n - 1 + REFIT_WARPS - 1) / REFIT_WARPS), dim3(REFIT_WARPS * 32), 0, st,
+    e = pdl_launch(k_refit_ranges, dim3((n - 1 + REFIT_WARPS - 1) / REFIT_WARPS + 1), dim3(REFIT_WARPS * 32), 0, st,
                    b.nodes, (const int2 *)range, (const float4 *)chunk1, (const float4 *)chunk2, n);
   return e != cudaSuccess ? e : cudaGetLastError();
 }

@@ -7,6 +7,10 @@ namespace mvp {
 
 constexpr int BVH_SORT_TILE = 2048;  // keys per radix-sort block (sizes BvhBuffers::counts)
 constexpr int BVH_SORT1_N = 8192;    // primitives up to which one block sorts the keys
+// The traversal's starting cut: up to 32 nodes that together cover every leaf, stored as
+// {count, node...} right after the last node; node arrays hold CUT_NODES extra nodes for it.
+constexpr int CUT_INTS = 33;
+constexpr int CUT_NODES = (CUT_INTS * 4 + 31) / 32;
 
 struct BvhBuffers {
   char *base = nullptr;
@@ -21,7 +25,7 @@ struct BvhBuffers {
   uint32_t *keys_a = nullptr, *keys_b = nullptr;  // Morton codes (sorted result in keys_a)
   int *vals_a = nullptr, *vals_b = nullptr;       // primitive ids (sorted result in vals_a)
   int *counts = nullptr;   // radix digit counts [256][blocks]
-  Node *nodes = nullptr;   // [2n-1]
+  Node *nodes = nullptr;   // [2n-1], then the traversal's starting cut (CUT_INTS ints at nodes + 2n-1)
   int *parent = nullptr;   // [2n]: the internal nodes' sorted leaf ranges (int2) during the build
   int *rank = nullptr;     // [n] each primitive's leaf position (its place in BVH order)
   float *gmc = nullptr;    // [n][12] adjoint accumulators of the march transform

@@ -41,7 +41,7 @@ constexpr size_t kOffValsA = align256(kOffKeysB + (size_t)kMaxPrims * sizeof(uin
 constexpr size_t kOffValsB = align256(kOffValsA + (size_t)kMaxPrims * sizeof(int));
 constexpr size_t kOffCounts = align256(kOffValsB + (size_t)kMaxPrims * sizeof(int));
 constexpr size_t kOffNodes = align256(kOffCounts + (size_t)256 * kMaxSortBlocks * sizeof(int));
-constexpr size_t kOffParent = align256(kOffNodes + (size_t)2 * kMaxPrims * sizeof(mvp::Node));
+constexpr size_t kOffParent = align256(kOffNodes + (size_t)(2 * kMaxPrims + mvp::CUT_NODES) * sizeof(mvp::Node));
 constexpr size_t kOffRank = align256(kOffParent + (size_t)2 * kMaxPrims * sizeof(int));
 constexpr size_t kBytes = align256(kOffRank + (size_t)kMaxPrims * sizeof(int));
 

@@ -234,9 +234,13 @@ __device__ __forceinline__ bool traverse_tile(SH &sh, const Node *__restrict__ n
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   if (n_prims <= 0) return true;
-  if (lane == 0) sh.stack[0] = 0;  // root: internal node 0, or leaf 0 when n == 1
+  // start from the cut the BVH build leaves after the last node: up to 32 nodes covering
+  // every leaf (the root alone for one primitive), all tested in the first step
+  const int *cut = reinterpret_cast<const int *>(nodes + 2 * n_prims - 1);
+  const int ncut = min(max(__ldg(cut), 1), 32);
+  if (lane < ncut) sh.stack[lane] = __ldg(cut + 1 + lane);
   __syncwarp();
-  int sp = 1, nc = 0;
+  int sp = ncut, nc = 0;
   while (true) {
     if (sp > 0 && nc < 32) {
       int take = sp < 32 ? sp : 32;
