@@ -8,7 +8,8 @@
 // 32 nodes per step, and collects candidate leaves. Each candidate is then tested
 // against every lane's ray with the exact FP32 slab test (Sec. 3.2.1: the list of
 // primitives each ray intersects), and kept if any lane hits it; the lane's hit
-// interval becomes an inclusive sample-index range [i_lo, i_hi] (packed 16+16 bits).
+// interval becomes an inclusive sample-index range [i_lo, i_hi] (stored as 8+8-bit
+// offsets from the entry's tile range start).
 #pragma once
 
 #include "bvh.cuh"

@@ -423,8 +423,9 @@ def test_tile_schedule_changes_no_result():
 
 
 def test_largest_sample_count_and_voxel_edge():
-    """The limits of the boundary: n_steps = MVP_MAX_STEPS (65535 samples, the largest
-    that the 16-bit sample ranges hold) and payload edge M = MVP_MAX_M (128)."""
+    """The limits of the boundary: n_steps = MVP_MAX_STEPS (65535 samples; the primitives'
+    sample spans exceed what a window's 8-bit lane offsets hold, so windows split) and payload
+    edge M = MVP_MAX_M (128)."""
     sc = synthetic.make_scene(8, 8, 3, layout="sphere", s_const=0.3, empty_frac=0.5)
     cam = synthetic.look_at_camera((0.0, 0.0, -3.0), 24, 20, 24.0)
     rays = synthetic.make_rays([cam], 0.0, 6.55345, 1e-4)
