@@ -10,12 +10,13 @@ namespace mvp {
 #endif
 constexpr int MARCH_CAP = MVP_MARCH_CAP;  // primitives a warp tile holds per depth window
 
-// Window capacity of the forward kernels by payload edge (MT, 0 = any): the smallest
-// voxel grids come with the most primitives per ray, where a longer list saves more
-// re-traversals than the L1 it takes costs (measured: 32768 primitives of 8^3, 64
+// Window capacity of the forward kernels by payload edge (MT: the edge fixed at compile
+// time; 0 = any edge; -1 = any edge up to 12, the serving kernels' small grids): the
+// smallest voxel grids come with the most primitives per ray, where a longer list saves
+// more re-traversals than the L1 it takes costs (measured: 32768 primitives of 8^3, 64
 // entries 6 % faster than 48; at 16^3 and 32^3, 48 is best).
 template <int MT>
-__host__ __device__ constexpr int march_cap() { return MT == 8 ? 64 : MARCH_CAP; }
+__host__ __device__ constexpr int march_cap() { return MT == 8 || MT == -1 ? 64 : MARCH_CAP; }
 
 #ifndef MVP_MARCH_MINB
 #define MVP_MARCH_MINB 5  // resident blocks per SM the march kernels are compiled for

@@ -115,20 +115,25 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, DT == MVP_F32 ? MVP_MARCH_MIN
 }
 
 // Kernel of a payload: dtype x {M = 8, 16, 32, other}.
-inline int serve_class(int dtype, int M) { return dtype * 4 + (M == 8 ? 0 : M == 16 ? 1 : M == 32 ? 2 : 3); }
-constexpr int SERVE_CLASSES = 12;
+// kernel class of an avatar: payload type x grid edge (8, 16, 32, another edge up to 12,
+// another edge)
+inline int serve_class(int dtype, int M) {
+  return dtype * 5 + (M == 8 ? 0 : M == 16 ? 1 : M == 32 ? 2 : M <= 12 ? 3 : 4);
+}
+constexpr int SERVE_CLASSES = 15;
 
 using ServeKernel = void (*)(const ServeReq);
 static const ServeKernel k_serve_table[SERVE_CLASSES] = {
-    k_serve<MVP_F32, 8>,  k_serve<MVP_F32, 16>,  k_serve<MVP_F32, 32>,  k_serve<MVP_F32, 0>,
-    k_serve<MVP_BF16, 8>, k_serve<MVP_BF16, 16>, k_serve<MVP_BF16, 32>, k_serve<MVP_BF16, 0>,
-    k_serve<MVP_F16, 8>,  k_serve<MVP_F16, 16>,  k_serve<MVP_F16, 32>,  k_serve<MVP_F16, 0>};
+    k_serve<MVP_F32, 8>,  k_serve<MVP_F32, 16>,  k_serve<MVP_F32, 32>,  k_serve<MVP_F32, -1>,  k_serve<MVP_F32, 0>,
+    k_serve<MVP_BF16, 8>, k_serve<MVP_BF16, 16>, k_serve<MVP_BF16, 32>, k_serve<MVP_BF16, -1>, k_serve<MVP_BF16, 0>,
+    k_serve<MVP_F16, 8>,  k_serve<MVP_F16, 16>,  k_serve<MVP_F16, 32>,  k_serve<MVP_F16, -1>,  k_serve<MVP_F16, 0>};
 // dynamic shared memory of each class's kernel (its window capacity depends on M)
 inline size_t serve_smem(int cls) {
-  switch (cls & 3) {
+  switch (cls % 5) {
     case 0: return sizeof(TileShared<march_cap<8>()>) * TILE_WARPS;
     case 1: return sizeof(TileShared<march_cap<16>()>) * TILE_WARPS;
     case 2: return sizeof(TileShared<march_cap<32>()>) * TILE_WARPS;
+    case 3: return sizeof(TileShared<march_cap<-1>()>) * TILE_WARPS;
     default: return sizeof(TileShared<march_cap<0>()>) * TILE_WARPS;
   }
 }
