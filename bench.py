@@ -1115,7 +1115,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serving-requests", type=int, default=2000, help="requests per arrival rate (0: skip)")
-    ap.add_argument("--serving-rates", default="50,100,200,400,1600", help="Poisson arrival rates, requests/s")
+    ap.add_argument("--serving-rates", default="50,100,200,400,800,1200,1600", help="Poisson arrival rates, requests/s")
     ap.add_argument("--serving-only", action="store_true", help="run only the serving measurement")
     ap.add_argument("--profile", action="store_true", help="render --frames frames of --workload, no timing")
     ap.add_argument("--workload", default=WORKLOAD)
