@@ -129,17 +129,11 @@ __device__ __forceinline__ void backward_tile(TileShared<CAP> &sh, const BwdArgs
           const float x0 = fmaf(ti, L.d[0], L.o[0]);
           const float x1 = fmaf(ti, L.d[1], L.o[1]);
           const float x2 = fmaf(ti, L.d[2], L.o[2]);
-          float ux = fmaf(X.r0.x, x0, fmaf(X.r0.y, x1, fmaf(X.r0.z, x2, X.r0.w)));
-          float uy = fmaf(X.r1.x, x0, fmaf(X.r1.y, x1, fmaf(X.r1.z, x2, X.r1.w)));
-          float uz = fmaf(X.r2.x, x0, fmaf(X.r2.y, x1, fmaf(X.r2.z, x2, X.r2.w)));
+          const float ux = fmaf(X.r0.x, x0, fmaf(X.r0.y, x1, fmaf(X.r0.z, x2, X.r0.w)));
+          const float uy = fmaf(X.r1.x, x0, fmaf(X.r1.y, x1, fmaf(X.r1.z, x2, X.r1.w)));
+          const float uz = fmaf(X.r2.x, x0, fmaf(X.r2.y, x1, fmaf(X.r2.z, x2, X.r2.w)));
           const bool kx = ux >= 0.0f && ux <= Mm1, ky = uy >= 0.0f && uy <= Mm1, kz = uz >= 0.0f && uz <= Mm1;
-          ux = fminf(fmaxf(ux, 0.0f), Mm1);
-          uy = fminf(fmaxf(uy, 0.0f), Mm1);
-          uz = fminf(fmaxf(uz, 0.0f), Mm1);
-          const int ix = min((int)ux, M - 2), iy = min((int)uy, M - 2), iz = min((int)uz, M - 2);
-          fx = ux - (float)ix;
-          fy = uy - (float)iy;
-          fz = uz - (float)iz;
+          const int ix = voxel_cell(ux, M - 2, fx), iy = voxel_cell(uy, M - 2, fy), iz = voxel_cell(uz, M - 2, fz);
           vo = iz * M2 + iy * M + ix;  // voxel within the primitive
           if (!MVP_IN_BOUNDS(vo >= 0 && vo + M2 + M + 1 < M2 * M, a.status)) continue;
           if (vo != held) {            // consecutive samples often stay in one cell

@@ -253,6 +253,17 @@ struct Voxel<MVP_F16> {
   }
 };
 
+// Cell and in-cell fraction along one axis of the voxel coordinate u (grid edge M,
+// Mm2 = M - 2): the values that clamping u into [0, M-1], truncating, capping the cell
+// at M - 2 and subtracting give, bit for bit, in four instructions instead of six. The
+// unsigned conversion sends u < 0 and NaN to cell 0; the saturated difference is then
+// 0 below the box (and for NaN) and 1 above it, as the clamped coordinate's would be.
+__device__ __forceinline__ int voxel_cell(float u, unsigned Mm2, float &f) {
+  const unsigned c = min(__float2uint_rz(u), Mm2);
+  asm("sub.rn.sat.f32 %0, %1, %2;" : "=f"(f) : "f"(u), "f"((float)c));
+  return (int)c;
+}
+
 __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float w) {
   return make_float4(fmaf(w, b.x - a.x, a.x), fmaf(w, b.y - a.y, a.y), fmaf(w, b.z - a.z, a.z),
                      fmaf(w, b.w - a.w, a.w));

@@ -36,10 +36,8 @@ __device__ __forceinline__ float4 sample_rgba(const Xform &X, const char *pbase,
   float ux = fmaf(X.r0.x, x[0], fmaf(X.r0.y, x[1], fmaf(X.r0.z, x[2], X.r0.w)));
   float uy = fmaf(X.r1.x, x[0], fmaf(X.r1.y, x[1], fmaf(X.r1.z, x[2], X.r1.w)));
   float uz = fmaf(X.r2.x, x[0], fmaf(X.r2.y, x[1], fmaf(X.r2.z, x[2], X.r2.w)));
-  ux = fminf(fmaxf(ux, 0.0f), Mm1);
-  uy = fminf(fmaxf(uy, 0.0f), Mm1);
-  uz = fminf(fmaxf(uz, 0.0f), Mm1);
-  const int ix = min((int)ux, M - 2), iy = min((int)uy, M - 2), iz = min((int)uz, M - 2);
+  float fx, fy, fz;
+  const int ix = voxel_cell(ux, M - 2, fx), iy = voxel_cell(uy, M - 2, fy), iz = voxel_cell(uz, M - 2, fz);
   const int v = (iz * M + iy) * M + ix;
   if (!MVP_IN_BOUNDS(v >= 0 && v + M * M + M + 1 < M * M * M, status)) return make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   const void *p = pbase;
@@ -47,7 +45,6 @@ __device__ __forceinline__ float4 sample_rgba(const Xform &X, const char *pbase,
   const float4 c010 = Voxel<DT>::load(p, v + M), c011 = Voxel<DT>::load(p, v + M + 1);
   const float4 c100 = Voxel<DT>::load(p, v + M * M), c101 = Voxel<DT>::load(p, v + M * M + 1);
   const float4 c110 = Voxel<DT>::load(p, v + M * M + M), c111 = Voxel<DT>::load(p, v + M * M + M + 1);
-  const float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
   const float2 wx = splat2(fx), nwx = splat2(-fx), wy = splat2(fy), nwy = splat2(-fy);
   const float4 c00 = lerp4x2(c000, c001, wx, nwx), c01 = lerp4x2(c010, c011, wx, nwx);
   const float4 c10 = lerp4x2(c100, c101, wx, nwx), c11 = lerp4x2(c110, c111, wx, nwx);
@@ -312,13 +309,11 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
           if (ii < lo || ii > hi) continue;
           // voxel coordinate u = Mx x + c (FP32, the cell decision of the oracle's
           // FP32 mode), clamped into the box
-          float ux = fmaf(X.r0.x, xs[c][0], fmaf(X.r0.y, xs[c][1], fmaf(X.r0.z, xs[c][2], X.r0.w)));
-          float uy = fmaf(X.r1.x, xs[c][0], fmaf(X.r1.y, xs[c][1], fmaf(X.r1.z, xs[c][2], X.r1.w)));
-          float uz = fmaf(X.r2.x, xs[c][0], fmaf(X.r2.y, xs[c][1], fmaf(X.r2.z, xs[c][2], X.r2.w)));
-          ux = fminf(fmaxf(ux, 0.0f), Mm1);
-          uy = fminf(fmaxf(uy, 0.0f), Mm1);
-          uz = fminf(fmaxf(uz, 0.0f), Mm1);
-          const int ix = min((int)ux, M - 2), iy = min((int)uy, M - 2), iz = min((int)uz, M - 2);
+          const float ux = fmaf(X.r0.x, xs[c][0], fmaf(X.r0.y, xs[c][1], fmaf(X.r0.z, xs[c][2], X.r0.w)));
+          const float uy = fmaf(X.r1.x, xs[c][0], fmaf(X.r1.y, xs[c][1], fmaf(X.r1.z, xs[c][2], X.r1.w)));
+          const float uz = fmaf(X.r2.x, xs[c][0], fmaf(X.r2.y, xs[c][1], fmaf(X.r2.z, xs[c][2], X.r2.w)));
+          float fx, fy, fz;
+          const int ix = voxel_cell(ux, M - 2, fx), iy = voxel_cell(uy, M - 2, fy), iz = voxel_cell(uz, M - 2, fz);
           const int v = (iz * M + iy) * M + ix;
           if (!MVP_IN_BOUNDS(v >= 0 && v + M * M + M + 1 < M * M * M, a.status)) continue;
           if (v != held) {
@@ -333,7 +328,6 @@ __device__ __forceinline__ void march_tile(TileShared<CAP> &sh, const MarchArgs 
             c111 = Voxel<DT>::load(p, v + M * M + M + 1);
             held = v;
           }
-          const float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
           const float2 wx = splat2(fx), nwx = splat2(-fx), wy = splat2(fy), nwy = splat2(-fy);
           const float2 wz = splat2(fz), nwz = splat2(-fz);
           const float4 c00 = lerp4x2(c000, c001, wx, nwx), c01 = lerp4x2(c010, c011, wx, nwx);
