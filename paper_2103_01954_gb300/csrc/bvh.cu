@@ -3,7 +3,8 @@
 // construction from sorted Morton codes).
 //
 // Steps, all on one stream without host synchronisation (for n <= BVH_SORT1_N steps
-// 1-3 are k_prims_partial and the one-block k_sort_one instead):
+// 1-3 are k_prims_partial and the one-block k_sort_one instead, for n <= BVH_SORTC_N
+// k_prims_partial and the one-cluster k_sort_cluster):
 //   1. k_bounds   : min/max of the centres (one block; exact).
 //   2. k_prims    : rotation, membership pose, march transform, oriented-box world
 //                   bounds, 30-bit Morton code of the centre.
@@ -13,6 +14,11 @@
 //                   unique keys (morton << 32 | k), one thread per node.
 //   5. refit      : each internal node's box as the union of the leaves in its sorted
 //                   range (k_refit_ranges), from 32- and 1024-leaf chunk unions.
+#include <cooperative_groups.h>
+
+#include <mutex>
+#include <unordered_map>
+
 #include "bvh.cuh"
 
 namespace mvp {
@@ -507,6 +513,147 @@ __global__ void __launch_bounds__(SORT1_THREADS) k_sort_one(const float *__restr
   }
 }
 
+// One-cluster sort for BVH_SORT1_N < n <= BVH_SORTC_N: the eight CTAs of a thread-block
+// cluster each hold a slice of 4096 (code, index) pairs in shared memory and run the
+// stable LSD radix of k_sort_one (3 passes of 10 bits) together. Per pass each CTA counts
+// its slice's digits, reads the other CTAs' counts through distributed shared memory to
+// place its keys after every lower digit and after the same digit in lower slices, and
+// stores each key straight into the slice that owns its new position. Two launches
+// (k_prims_partial and this) instead of the multi-block sort's fourteen.
+constexpr int SORTC_CTAS = 8;  // CTAs per cluster (the portable maximum)
+constexpr int SORTC_THREADS = 1024;
+constexpr int SORTC_SLICE = BVH_SORTC_N / SORTC_CTAS;
+// keys and values twice (this pass, next pass), per-warp digit counts [32][1024], and the
+// slice's digit counts, first positions and tile totals [1024] each
+constexpr size_t SORTC_SMEM =
+    sizeof(int) * ((size_t)4 * SORTC_SLICE + (size_t)(SORTC_THREADS / 32) * SORT1_BINS + (size_t)3 * SORT1_BINS);
+static_assert(SORTC_SLICE % SORTC_THREADS == 0 && SORTC_THREADS == SORT1_BINS, "one digit per thread");
+
+__global__ void __launch_bounds__(SORTC_THREADS) k_sort_cluster(const float *__restrict__ t, int n,
+                                                                const float *__restrict__ partial, int n_partial,
+                                                                float *__restrict__ scene_out,
+                                                                uint32_t *__restrict__ ka, int *__restrict__ va,
+                                                                int *status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint32_t *key0 = reinterpret_cast<uint32_t *>(smem_raw);
+  int *val0 = reinterpret_cast<int *>(key0 + SORTC_SLICE);
+  uint32_t *key1 = reinterpret_cast<uint32_t *>(val0 + SORTC_SLICE);
+  int *val1 = reinterpret_cast<int *>(key1 + SORTC_SLICE);
+  int(*wcnt)[SORT1_BINS] = reinterpret_cast<int(*)[SORT1_BINS]>(val1 + SORTC_SLICE);
+  int *hist = &wcnt[SORTC_THREADS / 32][0];  // this slice's digit counts (the other CTAs read them)
+  int *base = hist + SORT1_BINS;             // next position of each digit's keys from this slice
+  int *tile_total = base + SORT1_BINS;
+  __shared__ int wsum[32];
+  __shared__ float sscene[6];
+  pdl_wait();
+  pdl_trigger();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int r = (int)cluster.block_rank();
+  const int p0 = r * SORTC_SLICE;                       // the slice's first position
+  const int cnt = max(0, min(n - p0, SORTC_SLICE));     // keys in it
+  // centre bounds from the partials (each CTA reduces them), then the slice's codes
+  if (warp == 0 && lane < 6) {
+    float v = lane < 3 ? INFINITY : -INFINITY;
+    for (int b = 0; b < n_partial; ++b) v = lane < 3 ? fminf(v, partial[6 * b + lane]) : fmaxf(v, partial[6 * b + lane]);
+    sscene[lane] = v;
+    if (r == 0) scene_out[lane] = v;
+  }
+  __syncthreads();
+  const float sc[6] = {sscene[0], sscene[1], sscene[2], sscene[3], sscene[4], sscene[5]};
+  for (int i = tid; i < cnt; i += SORTC_THREADS) {
+    key0[i] = morton_code(t, p0 + i, sc);
+    val0[i] = p0 + i;
+  }
+  uint32_t *kin = key0, *kout = key1;
+  int *vin = val0, *vout = val1;
+  for (int pass = 0; pass < 3; ++pass) {
+    const int shift = SORT1_BITS * pass;
+    hist[tid] = 0;
+    __syncthreads();
+    for (int i = tid; i < cnt; i += SORTC_THREADS) atomicAdd(&hist[(kin[i] >> shift) & (SORT1_BINS - 1)], 1);
+    cluster.sync();  // every slice's counts are complete
+    // digit tid: its count over all slices, and in the slices before this one
+    int tot = 0, below = 0;
+#pragma unroll
+    for (int q = 0; q < SORTC_CTAS; ++q) {
+      const int h = cluster.map_shared_rank(hist, q)[tid];
+      tot += h;
+      below += q < r ? h : 0;
+    }
+    int incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const int w = wsum[lane];
+      int iw = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(FULL, iw, o);
+        if (lane >= o) iw += u;
+      }
+      wsum[lane] = iw - w;
+    }
+    __syncthreads();
+    base[tid] = wsum[warp] + incl - tot + below;
+    __syncthreads();
+    // stable scatter, one tile of 1024 keys at a time, in order
+    for (int t0 = 0; t0 < cnt; t0 += SORTC_THREADS) {
+      const int i = t0 + tid;
+      const bool valid = i < cnt;
+      const uint32_t key = valid ? kin[i] : 0u;
+      const int val = valid ? vin[i] : 0;
+      const int d = valid ? (int)((key >> shift) & (SORT1_BINS - 1)) : SORT1_BINS + lane;
+#pragma unroll 4
+      for (int w = 0; w < 32; ++w) wcnt[w][tid] = 0;
+      __syncthreads();
+      const unsigned peers = __match_any_sync(FULL, d);
+      const int rank = __popc(peers & lt);
+      if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+      __syncthreads();
+      int sum = 0;
+      for (int w = 0; w < 32; ++w) {
+        const int c = wcnt[w][tid];
+        wcnt[w][tid] = sum;
+        sum += c;
+      }
+      tile_total[tid] = sum;
+      __syncthreads();
+      if (valid) {
+        const int pos = base[d] + wcnt[warp][d] + rank;
+        if ((unsigned)pos < (unsigned)n) {
+          const int q = pos / SORTC_SLICE, li = pos - q * SORTC_SLICE;
+          cluster.map_shared_rank(kout, q)[li] = key;
+          cluster.map_shared_rank(vout, q)[li] = val;
+        } else if (status) {
+          atomicOr(status, STATUS_DEVICE);  // a position outside [0, n): never expected
+        }
+      }
+      __syncthreads();
+      base[tid] += tile_total[tid];
+      __syncthreads();
+    }
+    cluster.sync();  // every key of the pass is in its slice; the counts may be reused
+    uint32_t *tk = kin;
+    kin = kout;
+    kout = tk;
+    int *tv = vin;
+    vin = vout;
+    vout = tv;
+  }
+  for (int i = tid; i < cnt; i += SORTC_THREADS) {
+    ka[p0 + i] = kin[i];
+    va[p0 + i] = vin[i];
+  }
+}
+
 // ------------------------------------------------------------------ 4. hierarchy
 // Children of internal node i of the binary radix tree over n sorted unique 64-bit
 // keys (key(i) = morton << 32 | primitive): the direction of its range, its other
@@ -795,6 +942,38 @@ void bvh_release(BvhBuffers &b) {
   b = BvhBuffers();
 }
 
+// Whether the one-cluster sort can run in the current context: its dynamic shared memory
+// is opted in and the GPU can hold a cluster of eight such CTAs. Asked once per context
+// (allow_dynamic_smem remembers its opt-in per context; the answer is cached beside it).
+static bool cluster_sort_ready() {
+  if (allow_dynamic_smem(reinterpret_cast<const void *>(k_sort_cluster), SORTC_SMEM) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  static std::mutex mu;
+  static std::unordered_map<unsigned long long, bool> ready;
+  const unsigned long long ctx = current_context_id();
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = ready.find(ctx);
+  if (it != ready.end()) return it->second;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(SORTC_CTAS);
+  cfg.blockDim = dim3(SORTC_THREADS);
+  cfg.dynamicSmemBytes = SORTC_SMEM;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = SORTC_CTAS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  const bool ok = cudaOccupancyMaxActiveClusters(&clusters, k_sort_cluster, &cfg) == cudaSuccess && clusters >= 1;
+  if (!ok) cudaGetLastError();
+  ready[ctx] = ok;
+  return ok;
+}
+
 cudaError_t bvh_build(BvhBuffers &b, const float *t, const float *q, const float *s, int n, int M,
                       cudaStream_t st, int *status) {
   b.n = n;
@@ -812,6 +991,13 @@ cudaError_t bvh_build(BvhBuffers &b, const float *t, const float *q, const float
     // waits for it before touching memory)
     e = pdl_launch(k_sort_one, dim3(1), dim3(SORT1_THREADS), SORT1_SMEM, st, t, n, (const float *)partial,
                    n_partial, b.scene, b.keys_a, b.vals_a, b.keys_b, b.vals_b);
+    if (e != cudaSuccess) return e;
+  } else if (n <= BVH_SORTC_N && (size_t)6 * n_partial <= (size_t)256 * G && cluster_sort_ready()) {
+    // up to 32768: primitives with per-block bounds, then one cluster of eight CTAs sorts
+    float *partial = reinterpret_cast<float *>(b.counts);
+    k_prims_partial<<<n_partial, 256, 0, st>>>(t, q, s, n, M, b.pose, b.xf, b.pbox, partial, status);
+    cudaError_t e = cluster_launch(k_sort_cluster, dim3(SORTC_CTAS), dim3(SORTC_THREADS), SORTC_CTAS, SORTC_SMEM, st,
+                                   t, n, (const float *)partial, n_partial, b.scene, b.keys_a, b.vals_a, status);
     if (e != cudaSuccess) return e;
   } else {
     k_bounds<<<1, 1024, 0, st>>>(t, n, b.scene);

@@ -7,6 +7,7 @@ namespace mvp {
 
 constexpr int BVH_SORT_TILE = 2048;  // keys per radix-sort block (sizes BvhBuffers::counts)
 constexpr int BVH_SORT1_N = 8192;    // primitives up to which one block sorts the keys
+constexpr int BVH_SORTC_N = 32768;   // primitives up to which one thread-block cluster sorts them
 // The traversal's starting cut: up to 32 nodes that together cover every leaf, stored as
 // {count, node...} right after the last node; node arrays hold CUT_NODES extra nodes for it.
 constexpr int CUT_INTS = 33;

@@ -49,7 +49,8 @@ def _scene_n(n, seed=0, dup=False):
 
 
 @pytest.mark.parametrize("n,dup", [(1, False), (2, False), (3, False), (50, True), (513, False), (1000, "cluster"),
-                                   (4096, "cluster"), (5000, True), (8192, True), (8193, False), (40000, False)])
+                                   (4096, "cluster"), (5000, True), (8192, True), (8193, False), (12000, "cluster"),
+                                   (32768, True), (32769, False), (40000, False)])
 def test_bvh_keys_and_tree_bit_exact(n, dup):
     sc = _scene_n(n, dup=dup)
     rays = rays_from([0, 0, 3], [0, 0, -1], 1.0, 5.0, 0.01)
