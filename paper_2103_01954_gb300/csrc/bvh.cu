@@ -332,11 +332,15 @@ __global__ void __launch_bounds__(SORT1_THREADS) k_sort_one(const float *__restr
   const unsigned lt = (1u << lane) - 1u;
   // centre bounds from the partials, then the codes (into kb/vb: the odd pass count
   // ends in ka/va)
-  if (warp == 0 && lane < 6) {
-    float v = lane < 3 ? INFINITY : -INFINITY;
-    for (int b = 0; b < n_partial; ++b) v = lane < 3 ? fminf(v, partial[6 * b + lane]) : fmaxf(v, partial[6 * b + lane]);
-    sscene[lane] = v;
-    scene_out[lane] = v;
+  if (warp < 6) {  // warp j reduces component j, its lanes striding over the blocks
+    float v = warp < 3 ? INFINITY : -INFINITY;
+    for (int b = lane; b < n_partial; b += 32)
+      v = warp < 3 ? fminf(v, partial[6 * b + warp]) : fmaxf(v, partial[6 * b + warp]);
+    v = warp < 3 ? warp_min(v) : warp_max(v);
+    if (lane == 0) {
+      sscene[warp] = v;
+      scene_out[warp] = v;
+    }
   }
   __syncthreads();
   const float sc[6] = {sscene[0], sscene[1], sscene[2], sscene[3], sscene[4], sscene[5]};
@@ -514,20 +518,27 @@ __global__ void __launch_bounds__(SORT1_THREADS) k_sort_one(const float *__restr
 }
 
 // One-cluster sort for BVH_SORT1_N < n <= BVH_SORTC_N: the eight CTAs of a thread-block
-// cluster each hold a slice of 4096 (code, index) pairs in shared memory and run the
-// stable LSD radix of k_sort_one (3 passes of 10 bits) together. Per pass each CTA counts
-// its slice's digits, reads the other CTAs' counts through distributed shared memory to
-// place its keys after every lower digit and after the same digit in lower slices, and
-// stores each key straight into the slice that owns its new position. Two launches
-// (k_prims_partial and this) instead of the multi-block sort's fourteen.
+// cluster each hold a slice of 4096 (code, index) pairs in shared memory and run a stable
+// LSD radix sort together (4 passes of 8 bits). Per pass a CTA ranks its whole slice at
+// once (four keys per thread; per round and warp, the count of each digit), reads the
+// other CTAs' digit counts through distributed shared memory to place its keys after every
+// lower digit and after the same digit in lower slices, and stores each key straight into
+// the slice that owns its new position. Two launches (k_prims_partial and this) instead of
+// the multi-block sort's fourteen.
 constexpr int SORTC_CTAS = 8;  // CTAs per cluster (the portable maximum)
 constexpr int SORTC_THREADS = 1024;
-constexpr int SORTC_SLICE = BVH_SORTC_N / SORTC_CTAS;
-// keys and values twice (this pass, next pass), per-warp digit counts [32][1024], and the
-// slice's digit counts, first positions and tile totals [1024] each
-constexpr size_t SORTC_SMEM =
-    sizeof(int) * ((size_t)4 * SORTC_SLICE + (size_t)(SORTC_THREADS / 32) * SORT1_BINS + (size_t)3 * SORT1_BINS);
-static_assert(SORTC_SLICE % SORTC_THREADS == 0 && SORTC_THREADS == SORT1_BINS, "one digit per thread");
+constexpr int SORTC_SLICE = BVH_SORTC_N / SORTC_CTAS;        // keys per CTA
+constexpr int SORTC_ROUNDS = SORTC_SLICE / SORTC_THREADS;    // keys per thread
+constexpr int SORTC_BITS = 8, SORTC_BINS = 1 << SORTC_BITS, SORTC_PASSES = 4;  // 30-bit codes
+constexpr int SORTC_WARPS = SORTC_THREADS / 32;
+// keys and values twice (this pass, next pass), digit counts per round and warp, and per
+// digit the slice's count, first position, first staged place and each round's first rank
+constexpr size_t SORTC_SMEM = sizeof(int) * ((size_t)4 * SORTC_SLICE + (size_t)SORTC_ROUNDS * SORTC_WARPS * SORTC_BINS +
+                                             (size_t)(3 + SORTC_ROUNDS) * SORTC_BINS);
+static_assert(SORTC_ROUNDS * SORTC_WARPS * SORTC_BINS >= 2 * SORTC_SLICE, "the staged slice fits over the counts");
+static_assert(SORTC_SLICE == SORTC_ROUNDS * SORTC_THREADS && SORTC_ROUNDS * SORTC_BINS == SORTC_THREADS,
+              "one (round, digit) pair per thread in the count scan");
+static_assert(SORTC_BITS * SORTC_PASSES >= 30, "the passes cover the Morton code");
 
 __global__ void __launch_bounds__(SORTC_THREADS) k_sort_cluster(const float *__restrict__ t, int n,
                                                                 const float *__restrict__ partial, int n_partial,
@@ -541,25 +552,31 @@ __global__ void __launch_bounds__(SORTC_THREADS) k_sort_cluster(const float *__r
   int *val0 = reinterpret_cast<int *>(key0 + SORTC_SLICE);
   uint32_t *key1 = reinterpret_cast<uint32_t *>(val0 + SORTC_SLICE);
   int *val1 = reinterpret_cast<int *>(key1 + SORTC_SLICE);
-  int(*wcnt)[SORT1_BINS] = reinterpret_cast<int(*)[SORT1_BINS]>(val1 + SORTC_SLICE);
-  int *hist = &wcnt[SORTC_THREADS / 32][0];  // this slice's digit counts (the other CTAs read them)
-  int *base = hist + SORT1_BINS;             // next position of each digit's keys from this slice
-  int *tile_total = base + SORT1_BINS;
-  __shared__ int wsum[32];
+  // wcnt[j][w][d]: keys of digit d in round j, warp w (then their first rank in the round)
+  int(*wcnt)[SORTC_WARPS][SORTC_BINS] = reinterpret_cast<int(*)[SORTC_WARPS][SORTC_BINS]>(val1 + SORTC_SLICE);
+  int(*rbase)[SORTC_BINS] = reinterpret_cast<int(*)[SORTC_BINS]>(&wcnt[SORTC_ROUNDS][0][0]);  // [round][digit]
+  int *hist = &rbase[SORTC_ROUNDS][0];  // the slice's digit counts (the other CTAs read them)
+  int *base = hist + SORTC_BINS;        // each digit's first position for this slice's keys
+  int *lstart = base + SORTC_BINS;      // each digit's first place in the slice's staged order
+  __shared__ int wsum[SORTC_BINS / 32], lsum[SORTC_BINS / 32];
   __shared__ float sscene[6];
   pdl_wait();
   pdl_trigger();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const int r = (int)cluster.block_rank();
-  const int p0 = r * SORTC_SLICE;                       // the slice's first position
-  const int cnt = max(0, min(n - p0, SORTC_SLICE));     // keys in it
+  const int p0 = r * SORTC_SLICE;                    // the slice's first position
+  const int cnt = max(0, min(n - p0, SORTC_SLICE));  // keys in it
   // centre bounds from the partials (each CTA reduces them), then the slice's codes
-  if (warp == 0 && lane < 6) {
-    float v = lane < 3 ? INFINITY : -INFINITY;
-    for (int b = 0; b < n_partial; ++b) v = lane < 3 ? fminf(v, partial[6 * b + lane]) : fmaxf(v, partial[6 * b + lane]);
-    sscene[lane] = v;
-    if (r == 0) scene_out[lane] = v;
+  if (warp < 6) {  // warp j reduces component j, its lanes striding over the blocks
+    float v = warp < 3 ? INFINITY : -INFINITY;
+    for (int b = lane; b < n_partial; b += 32)
+      v = warp < 3 ? fminf(v, partial[6 * b + warp]) : fmaxf(v, partial[6 * b + warp]);
+    v = warp < 3 ? warp_min(v) : warp_max(v);
+    if (lane == 0) {
+      sscene[warp] = v;
+      if (r == 0) scene_out[warp] = v;
+    }
   }
   __syncthreads();
   const float sc[6] = {sscene[0], sscene[1], sscene[2], sscene[3], sscene[4], sscene[5]};
@@ -567,78 +584,119 @@ __global__ void __launch_bounds__(SORTC_THREADS) k_sort_cluster(const float *__r
     key0[i] = morton_code(t, p0 + i, sc);
     val0[i] = p0 + i;
   }
+  __syncthreads();
   uint32_t *kin = key0, *kout = key1;
   int *vin = val0, *vout = val1;
-  for (int pass = 0; pass < 3; ++pass) {
-    const int shift = SORT1_BITS * pass;
-    hist[tid] = 0;
+  for (int pass = 0; pass < SORTC_PASSES; ++pass) {
+    const int shift = SORTC_BITS * pass;
+    for (int x = tid; x < SORTC_ROUNDS * SORTC_WARPS * SORTC_BINS; x += SORTC_THREADS) (&wcnt[0][0][0])[x] = 0;
     __syncthreads();
-    for (int i = tid; i < cnt; i += SORTC_THREADS) atomicAdd(&hist[(kin[i] >> shift) & (SORT1_BINS - 1)], 1);
-    cluster.sync();  // every slice's counts are complete
-    // digit tid: its count over all slices, and in the slices before this one
-    int tot = 0, below = 0;
+    // round j holds positions j*1024 + tid, so (round, warp, lane) is the slice's order
+    uint32_t key[SORTC_ROUNDS];
+    int val[SORTC_ROUNDS], dig[SORTC_ROUNDS], rank[SORTC_ROUNDS];
 #pragma unroll
-    for (int q = 0; q < SORTC_CTAS; ++q) {
-      const int h = cluster.map_shared_rank(hist, q)[tid];
-      tot += h;
-      below += q < r ? h : 0;
-    }
-    int incl = tot;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int u = __shfl_up_sync(FULL, incl, o);
-      if (lane >= o) incl += u;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      const int w = wsum[lane];
-      int iw = w;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(FULL, iw, o);
-        if (lane >= o) iw += u;
-      }
-      wsum[lane] = iw - w;
-    }
-    __syncthreads();
-    base[tid] = wsum[warp] + incl - tot + below;
-    __syncthreads();
-    // stable scatter, one tile of 1024 keys at a time, in order
-    for (int t0 = 0; t0 < cnt; t0 += SORTC_THREADS) {
-      const int i = t0 + tid;
+    for (int j = 0; j < SORTC_ROUNDS; ++j) {
+      const int i = j * SORTC_THREADS + tid;
       const bool valid = i < cnt;
-      const uint32_t key = valid ? kin[i] : 0u;
-      const int val = valid ? vin[i] : 0;
-      const int d = valid ? (int)((key >> shift) & (SORT1_BINS - 1)) : SORT1_BINS + lane;
-#pragma unroll 4
-      for (int w = 0; w < 32; ++w) wcnt[w][tid] = 0;
-      __syncthreads();
-      const unsigned peers = __match_any_sync(FULL, d);
-      const int rank = __popc(peers & lt);
-      if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
-      __syncthreads();
+      key[j] = valid ? kin[i] : 0u;
+      val[j] = valid ? vin[i] : 0;
+      dig[j] = valid ? (int)((key[j] >> shift) & (SORTC_BINS - 1)) : -1 - lane;  // invalid: unique, no count
+      const unsigned peers = __match_any_sync(FULL, dig[j]);
+      rank[j] = __popc(peers & lt);
+      if (valid && rank[j] == 0) wcnt[j][warp][dig[j]] = __popc(peers);
+    }
+    __syncthreads();
+    {  // (round jr, digit dr): counts over the round's warps -> first rank per warp
+      const int jr = tid / SORTC_BINS, dr = tid % SORTC_BINS;
       int sum = 0;
-      for (int w = 0; w < 32; ++w) {
-        const int c = wcnt[w][tid];
-        wcnt[w][tid] = sum;
+      for (int w = 0; w < SORTC_WARPS; ++w) {
+        const int c = wcnt[jr][w][dr];
+        wcnt[jr][w][dr] = sum;
         sum += c;
       }
-      tile_total[tid] = sum;
-      __syncthreads();
-      if (valid) {
-        const int pos = base[d] + wcnt[warp][d] + rank;
-        if ((unsigned)pos < (unsigned)n) {
-          const int q = pos / SORTC_SLICE, li = pos - q * SORTC_SLICE;
-          cluster.map_shared_rank(kout, q)[li] = key;
-          cluster.map_shared_rank(vout, q)[li] = val;
-        } else if (status) {
-          atomicOr(status, STATUS_DEVICE);  // a position outside [0, n): never expected
-        }
+      rbase[jr][dr] = sum;  // the round's count, turned into its first rank below
+    }
+    __syncthreads();
+    if (tid < SORTC_BINS) {
+      int run = 0;
+#pragma unroll
+      for (int j = 0; j < SORTC_ROUNDS; ++j) {
+        const int c = rbase[j][tid];
+        rbase[j][tid] = run;
+        run += c;
       }
-      __syncthreads();
-      base[tid] += tile_total[tid];
-      __syncthreads();
+      hist[tid] = run;
+    }
+    cluster.sync();  // every slice's counts are complete
+    if (tid < SORTC_BINS) {
+      // digit tid: its count over all slices, and in the slices before this one
+      int tot = 0, below = 0;
+#pragma unroll
+      for (int q = 0; q < SORTC_CTAS; ++q) {
+        const int h = cluster.map_shared_rank(hist, q)[tid];
+        tot += h;
+        below += q < r ? h : 0;
+      }
+      int incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += u;
+      }
+      if (lane == 31) wsum[warp] = incl;
+      base[tid] = incl - tot + below;  // plus the lower warps' totals, below
+      const int own = hist[tid];
+      int lincl = own;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(FULL, lincl, o);
+        if (lane >= o) lincl += u;
+      }
+      if (lane == 31) lsum[warp] = lincl;
+      lstart[tid] = lincl - own;
+    }
+    __syncthreads();
+    if (tid < SORTC_BINS) {
+      int off = 0, loff = 0;
+      for (int w = 0; w < warp; ++w) {
+        off += wsum[w];
+        loff += lsum[w];
+      }
+      base[tid] += off;
+      lstart[tid] += loff;
+    }
+    __syncthreads();
+    // The keys in digit order within the slice (staged over the counts, which are read
+    // first), then each to the slice that owns its position: runs of one digit go to
+    // consecutive positions, so a warp's stores to another CTA's slice coalesce.
+    int lpos[SORTC_ROUNDS];
+#pragma unroll
+    for (int j = 0; j < SORTC_ROUNDS; ++j)
+      lpos[j] = dig[j] < 0 ? -1 : lstart[dig[j]] + rbase[j][dig[j]] + wcnt[j][warp][dig[j]] + rank[j];
+    __syncthreads();
+    uint32_t *stage_k = reinterpret_cast<uint32_t *>(&wcnt[0][0][0]);
+    int *stage_v = reinterpret_cast<int *>(stage_k + SORTC_SLICE);
+#pragma unroll
+    for (int j = 0; j < SORTC_ROUNDS; ++j) {
+      if ((unsigned)lpos[j] < (unsigned)cnt) {
+        stage_k[lpos[j]] = key[j];
+        stage_v[lpos[j]] = val[j];
+      } else if (dig[j] >= 0 && status) {
+        atomicOr(status, STATUS_DEVICE);  // a position outside the slice: never expected
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < cnt; i += SORTC_THREADS) {
+      const uint32_t k = stage_k[i];
+      const int d = (int)((k >> shift) & (SORTC_BINS - 1));
+      const int pos = base[d] + i - lstart[d];
+      if ((unsigned)pos < (unsigned)n) {
+        const int q = pos / SORTC_SLICE, li = pos - q * SORTC_SLICE;
+        cluster.map_shared_rank(kout, q)[li] = k;
+        cluster.map_shared_rank(vout, q)[li] = stage_v[i];
+      } else if (status) {
+        atomicOr(status, STATUS_DEVICE);  // a position outside [0, n): never expected
+      }
     }
     cluster.sync();  // every key of the pass is in its slice; the counts may be reused
     uint32_t *tk = kin;
