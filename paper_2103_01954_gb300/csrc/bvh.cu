@@ -522,9 +522,10 @@ __global__ void __launch_bounds__(SORT1_THREADS) k_sort_one(const float *__restr
 // LSD radix sort together (4 passes of 8 bits). Per pass a CTA ranks its whole slice at
 // once (four keys per thread; per round and warp, the count of each digit), reads the
 // other CTAs' digit counts through distributed shared memory to place its keys after every
-// lower digit and after the same digit in lower slices, and stores each key straight into
-// the slice that owns its new position. Two launches (k_prims_partial and this) instead of
-// the multi-block sort's fourteen.
+// lower digit and after the same digit in lower slices, stages its slice in digit order,
+// and stores each run of one digit into the slices that own those positions. Cluster
+// barriers separate the steps. Two launches (k_prims_partial and this) instead of the
+// multi-block sort's fourteen.
 constexpr int SORTC_CTAS = 8;  // CTAs per cluster (the portable maximum)
 constexpr int SORTC_THREADS = 1024;
 constexpr int SORTC_SLICE = BVH_SORTC_N / SORTC_CTAS;        // keys per CTA
