@@ -316,6 +316,7 @@ constexpr int SORT1_BUCKET_MAX = 64;  // largest bucket the insertion sort takes
 static_assert((2 * SORT1_BUCKETS + 2 * BVH_SORT1_N) * sizeof(int) <= SORT1_SMEM,
               "bucket arrays and the staged keys live in the digit-count area");
 static_assert(SORT1_BUCKETS % SORT1_THREADS == 0, "whole buckets per thread");
+static_assert(BVH_SORT1_N % SORT1_THREADS == 0, "whole keys per thread");
 
 __global__ void __launch_bounds__(SORT1_THREADS) k_sort_one(const float *__restrict__ t, int n,
                                                             const float *__restrict__ partial, int n_partial,
@@ -330,8 +331,9 @@ __global__ void __launch_bounds__(SORT1_THREADS) k_sort_one(const float *__restr
   pdl_trigger();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  // centre bounds from the partials, then the codes (into kb/vb: the odd pass count
-  // ends in ka/va)
+  // centre bounds from the partials, then the codes: held in registers (key k =
+  // tid + j * 1024 in code[j]), written to kb/vb only for the radix fallback (whose odd
+  // pass count ends in ka/va)
   if (warp < 6) {  // warp j reduces component j, its lanes striding over the blocks
     float v = warp < 3 ? INFINITY : -INFINITY;
     for (int b = lane; b < n_partial; b += 32)
@@ -344,11 +346,13 @@ __global__ void __launch_bounds__(SORT1_THREADS) k_sort_one(const float *__restr
   }
   __syncthreads();
   const float sc[6] = {sscene[0], sscene[1], sscene[2], sscene[3], sscene[4], sscene[5]};
-  for (int k = tid; k < n; k += SORT1_THREADS) {
-    kb[k] = morton_code(t, k, sc);
-    vb[k] = k;
+  constexpr int KPT = BVH_SORT1_N / SORT1_THREADS;  // keys per thread
+  uint32_t code[KPT];
+#pragma unroll
+  for (int j = 0; j < KPT; ++j) {
+    const int k = tid + j * SORT1_THREADS;
+    code[j] = k < n ? morton_code(t, k, sc) : 0u;
   }
-  __syncthreads();
 
   // Usual case: bucket by the top 13 code bits (atomic scatter), then sort each bucket
   // by (code, index) with insertion. The keys are unique, so this is the radix order.
@@ -359,7 +363,9 @@ __global__ void __launch_bounds__(SORT1_THREADS) k_sort_one(const float *__restr
     int *sv = reinterpret_cast<int *>(sk + BVH_SORT1_N);                // [n] their primitive indices
     for (int b = tid; b < SORT1_BUCKETS; b += SORT1_THREADS) cnt[b] = 0;
     __syncthreads();
-    for (int k = tid; k < n; k += SORT1_THREADS) atomicAdd(&cnt[kb[k] >> (30 - SORT1_BUCKET_BITS)], 1);
+#pragma unroll
+    for (int j = 0; j < KPT; ++j)
+      if (tid + j * SORT1_THREADS < n) atomicAdd(&cnt[code[j] >> (30 - SORT1_BUCKET_BITS)], 1);
     __syncthreads();
     // largest bucket, and this thread's 8 consecutive buckets' total
     constexpr int PER = SORT1_BUCKETS / SORT1_THREADS;
@@ -407,10 +413,12 @@ __global__ void __launch_bounds__(SORT1_THREADS) k_sort_one(const float *__restr
       }
       __syncthreads();
       // scatter into shared memory, sort each bucket there, then write out coalesced
-      for (int k = tid; k < n; k += SORT1_THREADS) {
-        const uint32_t key = kb[k];
-        const int pos = atomicAdd(&cur[key >> (30 - SORT1_BUCKET_BITS)], 1);
-        sk[pos] = key;
+#pragma unroll
+      for (int j = 0; j < KPT; ++j) {
+        const int k = tid + j * SORT1_THREADS;
+        if (k >= n) continue;
+        const int pos = atomicAdd(&cur[code[j] >> (30 - SORT1_BUCKET_BITS)], 1);
+        sk[pos] = code[j];
         sv[pos] = k;
       }
       __syncthreads();
@@ -439,6 +447,15 @@ __global__ void __launch_bounds__(SORT1_THREADS) k_sort_one(const float *__restr
     }
     __syncthreads();  // a bucket holds more than SORT1_BUCKET_MAX keys: stable radix below
   }
+#pragma unroll
+  for (int j = 0; j < KPT; ++j) {
+    const int k = tid + j * SORT1_THREADS;
+    if (k < n) {
+      kb[k] = code[j];
+      vb[k] = k;
+    }
+  }
+  __syncthreads();
 
   const uint32_t *kin = kb;
   const int *vin = vb;
@@ -717,11 +734,12 @@ __global__ void __launch_bounds__(SORTC_THREADS) k_sort_cluster(const float *__r
 // Children of internal node i of the binary radix tree over n sorted unique 64-bit
 // keys (key(i) = morton << 32 | primitive): the direction of its range, its other
 // end j, and the split (Karras). Children >= n-1 are leaves (n-1 + sorted index).
-template <class Key>
-__device__ __forceinline__ void internal_children(const Key &key, int n, int i, int &lc, int &rc, int &j_end) {
+// prefix(a, b) = the number of leading bits keys a and b share, for 0 <= a, b < n.
+template <class Prefix>
+__device__ __forceinline__ void internal_children(const Prefix &prefix, int n, int i, int &lc, int &rc, int &j_end) {
   auto delta = [&](int a, int b) -> int {
     if (b < 0 || b >= n) return -1;
-    return __clzll(key(a) ^ key(b));
+    return prefix(a, b);
   };
   int d = (delta(i, i + 1) - delta(i, i - 1)) >= 0 ? 1 : -1;
   int dmin = delta(i, i - d);
@@ -767,11 +785,13 @@ __device__ __forceinline__ void write_internal(Node *__restrict__ nodes, int i, 
 // (range[i]). Blocks of 1024 also union their leaves'
 // boxes in chunks of 32 (chunk1, one per warp) and 1024 (chunk2, one per block) for
 // the range refit.
-// STAGED (n <= HIER_STAGE_N): every block first copies the sorted keys into shared
-// memory, so the searches of the hierarchy read shared memory instead of L2.
+// STAGE 1 (n <= HIER_STAGE_N): every block first copies the sorted codes and primitive
+// indices into shared memory, so the searches of the hierarchy read shared memory
+// instead of L2. STAGE 2 (n <= BVH_SORTC_N): the codes alone (128 KB at most); the
+// indices, which only break ties between equal codes, are read from global memory.
 constexpr int HIER_THREADS = 1024;
 constexpr int HIER_STAGE_N = 8192;  // keys staged per block: 8 bytes each, 64 KB at most
-template <bool STAGED>
+template <int STAGE>
 __global__ void __launch_bounds__(HIER_THREADS) k_hierarchy(const uint32_t *__restrict__ km,
                                                             const int *__restrict__ kv, int n,
                                                             const float4 *__restrict__ pbox, Node *__restrict__ nodes,
@@ -780,13 +800,13 @@ __global__ void __launch_bounds__(HIER_THREADS) k_hierarchy(const uint32_t *__re
   __shared__ float sc[32][6];
   extern __shared__ __align__(16) unsigned char hier_smem[];
   uint32_t *skm = reinterpret_cast<uint32_t *>(hier_smem);
-  int *skv = reinterpret_cast<int *>(hier_smem + sizeof(uint32_t) * (STAGED ? n : 0));
+  int *skv = reinterpret_cast<int *>(hier_smem + sizeof(uint32_t) * (STAGE > 0 ? n : 0));
   pdl_wait();
   pdl_trigger();
-  if (STAGED) {
+  if (STAGE > 0) {
     for (int a = threadIdx.x; a < n; a += HIER_THREADS) {
       skm[a] = km[a];
-      skv[a] = kv[a];
+      if (STAGE == 1) skv[a] = kv[a];
     }
     __syncthreads();
   }
@@ -832,11 +852,19 @@ __global__ void __launch_bounds__(HIER_THREADS) k_hierarchy(const uint32_t *__re
     cut[1] = 0;
   }
   if (i >= n - 1) return;
-  auto key = [&](int a) -> uint64_t {
-    return STAGED ? ((uint64_t)skm[a] << 32) | (uint32_t)skv[a] : ((uint64_t)km[a] << 32) | (uint32_t)kv[a];
+  auto prefix = [&](int a, int b) -> int {
+    if (STAGE == 2) {  // codes first; equal codes share 32 bits and then those of the indices
+      const uint32_t ca = skm[a], cb = skm[b];
+      return ca != cb ? __clz((int)(ca ^ cb)) : 32 + __clz((int)((uint32_t)kv[a] ^ (uint32_t)kv[b]));
+    }
+    const uint64_t ka = STAGE == 1 ? ((uint64_t)skm[a] << 32) | (uint32_t)skv[a]
+                                   : ((uint64_t)km[a] << 32) | (uint32_t)kv[a];
+    const uint64_t kb = STAGE == 1 ? ((uint64_t)skm[b] << 32) | (uint32_t)skv[b]
+                                   : ((uint64_t)km[b] << 32) | (uint32_t)kv[b];
+    return __clzll(ka ^ kb);
   };
   int lc, rc, j;
-  internal_children(key, n, i, lc, rc, j);
+  internal_children(prefix, n, i, lc, rc, j);
   write_internal(nodes, i, lc, rc);
   range[i] = make_int2(min(i, j), max(i, j));
 }
@@ -1078,16 +1106,24 @@ cudaError_t bvh_build(BvhBuffers &b, const float *t, const float *q, const float
   // second key and value buffers (n/32 and n/1024 boxes of 32 bytes fit in 4n bytes)
   int2 *range = reinterpret_cast<int2 *>(b.parent);
   float4 *chunk1 = reinterpret_cast<float4 *>(b.keys_b), *chunk2 = reinterpret_cast<float4 *>(b.vals_b);
-  const bool staged = n <= HIER_STAGE_N;
-  const size_t hsmem = staged ? (size_t)n * 8 : 0;
-  cudaError_t e = staged ? allow_dynamic_smem(reinterpret_cast<const void *>(k_hierarchy<true>), hsmem) : cudaSuccess;
-  if (e == cudaSuccess)
-    e = staged ? pdl_launch(k_hierarchy<true>, dim3((n + HIER_THREADS - 1) / HIER_THREADS), dim3(HIER_THREADS), hsmem,
-                            st, (const uint32_t *)b.keys_a, (const int *)b.vals_a, n, (const float4 *)b.pbox, b.nodes,
-                            range, chunk1, chunk2, b.rank)
-               : pdl_launch(k_hierarchy<false>, dim3((n + HIER_THREADS - 1) / HIER_THREADS), dim3(HIER_THREADS), 0, st,
-                            (const uint32_t *)b.keys_a, (const int *)b.vals_a, n, (const float4 *)b.pbox, b.nodes,
-                            range, chunk1, chunk2, b.rank);
+  const int stage = n <= HIER_STAGE_N ? 1 : (n <= BVH_SORTC_N ? 2 : 0);
+  const size_t hsmem = stage == 1 ? (size_t)n * 8 : (stage == 2 ? (size_t)n * 4 : 0);
+  const dim3 hgrid((n + HIER_THREADS - 1) / HIER_THREADS), hblock(HIER_THREADS);
+  cudaError_t e = cudaSuccess;
+  if (stage == 1) {
+    e = allow_dynamic_smem(reinterpret_cast<const void *>(k_hierarchy<1>), hsmem);
+    if (e == cudaSuccess)
+      e = pdl_launch(k_hierarchy<1>, hgrid, hblock, hsmem, st, (const uint32_t *)b.keys_a, (const int *)b.vals_a, n,
+                     (const float4 *)b.pbox, b.nodes, range, chunk1, chunk2, b.rank);
+  } else if (stage == 2) {
+    e = allow_dynamic_smem(reinterpret_cast<const void *>(k_hierarchy<2>), hsmem);
+    if (e == cudaSuccess)
+      e = pdl_launch(k_hierarchy<2>, hgrid, hblock, hsmem, st, (const uint32_t *)b.keys_a, (const int *)b.vals_a, n,
+                     (const float4 *)b.pbox, b.nodes, range, chunk1, chunk2, b.rank);
+  } else {
+    e = pdl_launch(k_hierarchy<0>, hgrid, hblock, 0, st, (const uint32_t *)b.keys_a, (const int *)b.vals_a, n,
+                   (const float4 *)b.pbox, b.nodes, range, chunk1, chunk2, b.rank);
+  }
   if (e == cudaSuccess && n > 1)
     e = pdl_launch(k_refit_ranges, dim3((n - 1 + REFIT_WARPS - 1) / REFIT_WARPS + 1), dim3(REFIT_WARPS * 32), 0, st,
                    b.nodes, (const int2 *)range, (const float4 *)chunk1, (const float4 *)chunk2, n);
